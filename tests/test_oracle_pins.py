@@ -1,0 +1,499 @@
+"""Pins of the FP64 oracle against facts fixed by physics and mathematics.
+
+The paper prints no formula and no worked example (section 2 only names
+propagateToZ / propagateToR / KalmanUpdate), so every pin here comes from
+outside the oracle: textbook circle geometry, an independent Runge-Kutta
+integration of the Lorentz force, straight-line limits, finite differences,
+the information form and generalised least squares of the Kalman update,
+and the chi-square / pull statistics of a correctly specified filter.
+Each is chosen so that a plausible slip (sign of the curvature, the unit
+constant, a dropped Jacobian term, a transposed gain) fails at least one.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2401_14221_gb300 import workload as W
+
+BZ = 3.8
+# Curvature constant from the speed of light (independent of the oracle's).
+KAPPA_UNIT = W.GEV_PER_T_CM
+
+
+def omega_of(q, k, bz=BZ):
+    # Signed turning rate d(phi)/ds from F = q v x B with B = +z:
+    # a positive charge turns clockwise, i.e. phi decreases.
+    return -q * KAPPA_UNIT * bz * k
+
+
+def angle_diff(a, b):
+    return (a - b + math.pi) % (2 * math.pi) - math.pi
+
+
+def sample_tracks(n=64, seed=11, pt=(0.3, 20.0), eta=(-2.0, 2.0)):
+    rng = np.random.default_rng(seed)
+    out = []
+    for _ in range(n):
+        x, y = rng.normal(0, 0.5, 2)
+        z = rng.normal(0, 5)
+        k = 1.0 / rng.uniform(*pt)
+        phi = rng.uniform(-math.pi, math.pi)
+        th = 2 * math.atan(math.exp(-rng.uniform(*eta)))
+        q = 1 if rng.random() < 0.5 else -1
+        out.append((np.array([x, y, z, k, phi, th]), q))
+    return out
+
+
+# ------------------------------------------------------------------ P1, P2
+
+@pytest.mark.parametrize("zt", [50.0, -30.0, 120.0])
+def test_p2z_lands_on_plane_and_helix(zt):
+    for p, q in sample_tracks():
+        po, J, st = oracle.propagate_to_z(p, q, BZ, zt)
+        assert st == 0
+        assert po[2] == zt  # on the plane, exactly
+        w = omega_of(q, p[3])
+        cx, cy = p[0] - math.sin(p[4]) / w, p[1] + math.cos(p[4]) / w
+        rad = math.hypot(po[0] - cx, po[1] - cy)
+        assert abs(rad * abs(w) - 1.0) < 1e-11
+
+
+@pytest.mark.parametrize("R", [4.0, 30.0, 60.0])
+def test_p2r_lands_on_cylinder_and_helix(R):
+    n_hit = 0
+    for p, q in sample_tracks(pt=(0.5, 50.0)):
+        po, J, st = oracle.propagate_to_r(p, q, BZ, R)
+        if st:
+            continue
+        n_hit += 1
+        assert abs(math.hypot(po[0], po[1]) - R) <= 1e-12 * R
+        w = omega_of(q, p[3])
+        cx, cy = p[0] - math.sin(p[4]) / w, p[1] + math.cos(p[4]) / w
+        assert abs(math.hypot(po[0] - cx, po[1] - cy) * abs(w) - 1.0) < 1e-11
+        # first crossing: the radius grows monotonically up to the surface
+        s = oracle.path_to_r(p, q, BZ, R)
+        for f in np.linspace(0.05, 0.95, 7):
+            mid = oracle.helix_at(p, q, BZ, f * s)
+            assert math.hypot(mid[0], mid[1]) < R
+    assert n_hit > 40
+
+
+# ---------------------------------------------------------------------- P3
+
+def test_p2z_matches_runge_kutta_lorentz_force():
+    for p, q in sample_tracks(n=12, seed=3, eta=(0.8, 2.5)):
+        zt = p[2] + 40.0
+        po, _, st = oracle.propagate_to_z(p, q, BZ, zt)
+        assert st == 0
+        truth, _ = W.simulate_to_z(p.reshape(6, 1), np.array([q]), BZ, zt, steps=4000)
+        assert abs(po[0] - truth[0, 0]) < 1e-8
+        assert abs(po[1] - truth[1, 0]) < 1e-8
+        assert abs(angle_diff(po[4], truth[4, 0])) < 1e-9
+
+
+def test_p2r_matches_runge_kutta_lorentz_force():
+    for p, q in sample_tracks(n=8, seed=5, pt=(0.6, 30.0)):
+        R = 25.0
+        po, _, st = oracle.propagate_to_r(p, q, BZ, R)
+        truth, s, reached = W.simulate_to_r(p.reshape(6, 1), np.array([q]), BZ, R, h=0.01,
+                                            bisect=60)
+        assert bool(reached[0]) == (st == 0)
+        if st:
+            continue
+        assert np.max(np.abs(po[:3] - truth[:3, 0])) < 1e-8
+        assert abs(angle_diff(po[4], truth[4, 0])) < 1e-9
+
+
+# ------------------------------------------------------- textbook geometry
+
+def test_p2z_quarter_turn_closed_form():
+    # Start at the origin along +x, positive charge: clockwise circle of
+    # radius rho centred at (0, -rho).  A quarter turn ends at (rho, -rho)
+    # heading along -y.
+    rho = 100.0
+    k = 1.0 / (KAPPA_UNIT * BZ * rho)
+    th = 1.0
+    s = 0.5 * math.pi * rho
+    zt = s / math.tan(th)
+    po, _, st = oracle.propagate_to_z([0, 0, 0, k, 0.0, th], 1, BZ, zt)
+    assert st == 0
+    assert abs(po[0] - rho) < 1e-10 and abs(po[1] + rho) < 1e-10
+    assert abs(po[4] + 0.5 * math.pi) < 1e-12
+
+
+def test_p2r_chord_closed_form():
+    # From the origin the crossing of radius R is at chord length R on a
+    # circle of radius rho: turning angle a = 2 asin(R / (2 rho)), position at
+    # azimuth -a/2 (clockwise), path rho * a.
+    rho, R, th = 80.0, 30.0, 1.2
+    k = 1.0 / (KAPPA_UNIT * BZ * rho)
+    a = 2 * math.asin(R / (2 * rho))
+    po, _, st = oracle.propagate_to_r([0, 0, 1.0, k, 0.0, th], 1, BZ, R)
+    assert st == 0
+    assert abs(po[0] - R * math.cos(a / 2)) < 1e-11
+    assert abs(po[1] + R * math.sin(a / 2)) < 1e-11
+    assert abs(po[2] - (1.0 + rho * a / math.tan(th))) < 1e-11
+    assert abs(po[4] + a) < 1e-12
+    # negative charge mirrors y and phi
+    po2, _, _ = oracle.propagate_to_r([0, 0, 1.0, k, 0.0, th], -1, BZ, R)
+    assert abs(po2[1] - R * math.sin(a / 2)) < 1e-11 and abs(po2[4] - a) < 1e-12
+
+
+# ---------------------------------------------------------------------- P4
+
+@pytest.mark.parametrize("k,bz", [(0.0, BZ), (1e-13, BZ), (0.5, 0.0)])
+def test_straight_line_limit(k, bz):
+    for p, q in sample_tracks(n=16, seed=7):
+        p = p.copy()
+        p[3] = k
+        x0 = p[:3]
+        d = np.array([math.sin(p[5]) * math.cos(p[4]), math.sin(p[5]) * math.sin(p[4]),
+                      math.cos(p[5])])
+        # line-plane intersection
+        zt = x0[2] + 25.0
+        t = (zt - x0[2]) / d[2]
+        exp = x0 + t * d
+        po, _, st = oracle.propagate_to_z(p, q, bz, zt)
+        assert st == 0
+        assert np.max(np.abs(po[:3] - exp)) < 1e-9 * (1 + abs(t))
+        assert abs(angle_diff(po[4], p[4])) < 1e-12
+        # line-cylinder intersection (positive root of the quadratic)
+        R = 40.0
+        dt = d[:2] / np.linalg.norm(d[:2])
+        b = x0[:2] @ dt
+        c = x0[:2] @ x0[:2] - R * R
+        sT = -b + math.sqrt(b * b - c)
+        exp2 = x0[:2] + sT * dt
+        po2, _, st2 = oracle.propagate_to_r(p, q, bz, R)
+        assert st2 == 0
+        assert np.max(np.abs(po2[:2] - exp2)) < 1e-9
+        assert abs(po2[2] - (x0[2] + sT / math.tan(p[5]))) < 1e-9
+
+
+# ---------------------------------------------------------------------- P5
+
+def test_full_turn_returns_to_start():
+    for p, q in sample_tracks(n=16, seed=9, pt=(0.5, 3.0)):
+        w = omega_of(q, p[3])
+        s = 2 * math.pi / abs(w)
+        zt = p[2] + s / math.tan(p[5])
+        po, _, st = oracle.propagate_to_z(p, q, BZ, zt)
+        assert st == 0
+        assert abs(po[0] - p[0]) < 1e-9 * s
+        assert abs(po[1] - p[1]) < 1e-9 * s
+        assert abs(angle_diff(po[4], p[4])) < 1e-9
+
+
+# ---------------------------------------------------------------------- P6
+
+def _fd_jacobian(fn, p, eps):
+    """Central differences with one Richardson step (error O(eps^4))."""
+    J = np.zeros((6, 6))
+    base = fn(p)
+    for j in range(6):
+        def d(e):
+            pp, pm = p.copy(), p.copy()
+            pp[j] += e
+            pm[j] -= e
+            fp, fm = fn(pp), fn(pm)
+            diff = fp - fm
+            diff[4] = angle_diff(fp[4], fm[4])
+            return diff / (2 * e)
+        J[:, j] = (4 * d(eps[j] / 2) - d(eps[j])) / 3
+    return J, base
+
+
+def _eps(p):
+    return np.array([1e-3, 1e-3, 1e-3, 1e-3 * p[3], 1e-4, 1e-4])
+
+
+@pytest.mark.parametrize("zt", [60.0, -20.0])
+def test_p2z_jacobian_matches_finite_differences(zt):
+    for p, q in sample_tracks(n=24, seed=13, pt=(0.3, 80.0), eta=(0.5, 2.5)):
+        _, J, st = oracle.propagate_to_z(p, q, BZ, zt)
+        assert st == 0
+        Jfd, _ = _fd_jacobian(lambda x: oracle.propagate_to_z(x, q, BZ, zt)[0], p, _eps(p))
+        err = np.abs(J - Jfd) / np.maximum(1.0, np.abs(J))
+        assert err.max() < 1e-7, (err.max(), np.unravel_index(err.argmax(), err.shape))
+
+
+@pytest.mark.parametrize("R", [30.0, 7.0])
+def test_p2r_jacobian_matches_finite_differences(R):
+    n = 0
+    for p, q in sample_tracks(n=24, seed=17, pt=(0.6, 80.0)):
+        p = p.copy()
+        p[0] *= 0.1
+        p[1] *= 0.1
+        _, J, st = oracle.propagate_to_r(p, q, BZ, R)
+        if st:
+            continue
+        n += 1
+        Jfd, _ = _fd_jacobian(lambda x: oracle.propagate_to_r(x, q, BZ, R)[0], p, _eps(p))
+        err = np.abs(J - Jfd) / np.maximum(1.0, np.abs(J))
+        assert err.max() < 1e-7, (err.max(), np.unravel_index(err.argmax(), err.shape))
+    assert n > 15
+
+
+# ---------------------------------------------------------------------- P7
+
+def test_p2z_jacobian_chain_rule():
+    for p, q in sample_tracks(n=16, seed=19, eta=(0.8, 2.5)):
+        z1, z2 = p[2] + 20.0, p[2] + 55.0
+        p1, J01, _ = oracle.propagate_to_z(p, q, BZ, z1)
+        _, J12, _ = oracle.propagate_to_z(p1, q, BZ, z2)
+        p2, J02, _ = oracle.propagate_to_z(p, q, BZ, z2)
+        comp = J12 @ J01
+        assert np.max(np.abs(comp - J02) / np.maximum(1, np.abs(J02))) < 1e-10
+
+
+def test_p2r_jacobian_chain_rule():
+    for p, q in sample_tracks(n=16, seed=21, pt=(1.0, 50.0)):
+        p = p.copy()
+        p[:2] *= 0.1
+        p1, J01, s1 = oracle.propagate_to_r(p, q, BZ, 10.0)
+        p2, J02, s2 = oracle.propagate_to_r(p, q, BZ, 35.0)
+        if s1 or s2:
+            continue
+        _, J12, s3 = oracle.propagate_to_r(p1, q, BZ, 35.0)
+        assert s3 == 0
+        comp = J12 @ J01
+        assert np.max(np.abs(comp - J02) / np.maximum(1, np.abs(J02))) < 1e-9
+
+
+# ---------------------------------------------------------------------- P8
+
+def test_p2z_zero_distance_jacobian():
+    # At zero distance the Jacobian is the projection along the track onto
+    # the plane: the identity, except that a shift in z moves the crossing
+    # point by -tan(theta) along the transverse direction, and the z row is 0.
+    for p, q in sample_tracks(n=8, seed=23):
+        po, J, st = oracle.propagate_to_z(p, q, BZ, p[2])
+        assert st == 0
+        t = math.tan(p[5])
+        w = omega_of(q, p[3])
+        exp = np.eye(6)
+        exp[2, :] = 0.0
+        exp[0, 2] = -t * math.cos(p[4])
+        exp[1, 2] = -t * math.sin(p[4])
+        exp[4, 2] = -t * w
+        assert np.max(np.abs(J - exp)) < 1e-12
+        assert np.max(np.abs(po[[0, 1, 3, 5]] - p[[0, 1, 3, 5]])) == 0.0
+
+
+# ------------------------------------------------------------ update pins
+
+def random_spd(rng, scale):
+    A = rng.standard_normal((6, 6))
+    C = A @ A.T * 0.05 + np.eye(6)
+    return C * np.outer(scale, scale)
+
+
+def pack(C):
+    return np.array([C[i, j] for i in range(6) for j in range(i + 1)])
+
+
+def unpack(c):
+    C = np.zeros((6, 6))
+    idx = 0
+    for i in range(6):
+        for j in range(i + 1):
+            C[i, j] = C[j, i] = c[idx]
+            idx += 1
+    return C
+
+
+SCALE = np.array([0.03, 0.03, 0.1, 0.01, 2e-3, 2e-3])
+
+
+def update_cases(n=20, seed=31):
+    rng = np.random.default_rng(seed)
+    for _ in range(n):
+        C = random_spd(rng, SCALE)
+        p = np.array([20.0, -5.0, 30.0, 0.5, 0.3, 1.1]) + rng.standard_normal(6) * SCALE
+        ang = rng.uniform(-math.pi, math.pi)
+        H = np.zeros((2, 6))
+        if rng.random() < 0.5:
+            H[0, 0] = H[1, 1] = 1.0
+        else:
+            H[0, 0], H[0, 1], H[1, 2] = -math.sin(ang), math.cos(ang), 1.0
+        a = rng.standard_normal((2, 2)) * 0.01
+        V = a @ a.T + np.diag([1e-4, 2e-4])
+        r = rng.standard_normal(2) * 0.02
+        yield p, C, H, V, r
+
+
+def test_update_information_form_and_gls():
+    # P9 / P14: the Kalman update equals the generalised least-squares fit of
+    # the prior and the measurement, (C^-1 + H^T V^-1 H) p = C^-1 p' + H^T V^-1 m,
+    # and its covariance is the inverse of the information matrix.
+    for p, C, H, V, r in update_cases():
+        po, co, chi2, st = oracle.kalman_update(p, pack(C), H.ravel(), [V[0, 0], V[0, 1], V[1, 1]], r)
+        assert st == 0
+        m = H @ p + r
+        Ci, Vi = np.linalg.inv(C), np.linalg.inv(V)
+        info = Ci + H.T @ Vi @ H
+        p_gls = np.linalg.solve(info, Ci @ p + H.T @ Vi @ m)
+        C_gls = np.linalg.inv(info)
+        d = po - p_gls
+        d[4] = angle_diff(po[4], p_gls[4])
+        assert np.max(np.abs(d) / SCALE) < 1e-9
+        Co = unpack(co)
+        assert np.max(np.abs(Co - C_gls) / np.outer(SCALE, SCALE)) < 1e-9
+        np.linalg.cholesky(Co)  # positive definite
+        S = H @ C @ H.T + V
+        assert abs(chi2 - r @ np.linalg.solve(S, r)) < 1e-10 * (1 + chi2)
+
+
+def test_update_joseph_equals_standard():
+    for p, C, H, V, r in update_cases(seed=33):
+        v3 = [V[0, 0], V[0, 1], V[1, 1]]
+        po1, co1, _, _ = oracle.kalman_update(p, pack(C), H.ravel(), v3, r, oracle.FORM_STANDARD)
+        po2, co2, _, _ = oracle.kalman_update(p, pack(C), H.ravel(), v3, r, oracle.FORM_JOSEPH)
+        assert np.max(np.abs(po1 - po2)) == 0.0
+        C1, C2 = unpack(co1), unpack(co2)
+        assert np.max(np.abs(C1 - C2) / np.outer(SCALE, SCALE)) < 1e-10
+
+
+def test_update_exact_measurement_limit():
+    # P10: V -> 0 puts the measured combinations on the measurement.
+    for p, C, H, V, r in update_cases(seed=35):
+        po, _, _, st = oracle.kalman_update(p, pack(C), H.ravel(), [1e-22, 0.0, 1e-22], r)
+        assert st == 0
+        assert np.max(np.abs(H @ po - (H @ p + r))) < 1e-9
+
+
+def test_update_uninformative_measurement_limit():
+    # P11: V -> infinity leaves the prediction unchanged.
+    for p, C, H, V, r in update_cases(seed=37):
+        po, co, _, st = oracle.kalman_update(p, pack(C), H.ravel(), [1e14, 0.0, 1e14], r)
+        assert np.max(np.abs(po - p) / SCALE) < 1e-9
+        assert np.max(np.abs(unpack(co) - C) / np.outer(SCALE, SCALE)) < 1e-9
+
+
+def test_update_one_dimensional_textbook():
+    # P12: with the second measurement row made uninformative the update is the
+    # scalar textbook filter on x: K = C e_x / (C_xx + V_xx).
+    for p, C, _, V, r in update_cases(seed=39):
+        H = np.zeros((2, 6))
+        H[0, 0] = H[1, 1] = 1.0
+        po, co, _, _ = oracle.kalman_update(p, pack(C), H.ravel(), [V[0, 0], 0.0, 1e40], r)
+        K = C[:, 0] / (C[0, 0] + V[0, 0])
+        exp_p = p + K * r[0]
+        exp_C = C - np.outer(K, C[0, :])
+        d = po - exp_p
+        d[4] = angle_diff(po[4], exp_p[4])
+        assert np.max(np.abs(d) / SCALE) < 1e-10
+        assert np.max(np.abs(unpack(co) - exp_C) / np.outer(SCALE, SCALE)) < 1e-10
+
+
+def test_propagated_covariance_is_psd_and_degenerate_on_surface():
+    # After propagation to a plane (cylinder) the covariance has no extent
+    # across the surface: rank 5; after the update it stays positive
+    # semi-definite and symmetric.
+    w = W.make_p2r(1, 200, seed=5)
+    st, cv, stat, _ = oracle.step_batch(oracle.P2R, w.state.T, w.cov.T, w.charge, w.hit.T,
+                                        w.hitcov.T, w.surf, w.bz)
+    for i in range(50):
+        C = unpack(cv[i])
+        ev = np.linalg.eigvalsh(C / np.sqrt(np.outer(np.diag(C), np.diag(C))))
+        assert ev.min() > -1e-9
+        # the update moves the state only within the surface: the radial
+        # direction at the propagated point carries no variance
+        pp, _, _ = oracle.propagate_to_r(w.state[:, i], int(w.charge[i]), w.bz, w.surf)
+        nrm = np.array([pp[0], pp[1], 0, 0, 0, 0]) / w.surf
+        assert abs(nrm @ C @ nrm) < 1e-12 * np.trace(C)
+
+
+# ------------------------------------------------------------ statistics
+
+@pytest.mark.parametrize("kind", [oracle.P2Z, oracle.P2R])
+def test_chi2_and_pull_statistics(kind):
+    # P13: inputs are the truth smeared by N(0, C) and hits are the true
+    # crossing smeared by N(0, V): the filter is correctly specified, so the
+    # chi-square has mean 2 (two measured coordinates) and the pulls of the
+    # updated state against the true state on the surface are N(0, 1).
+    if kind == oracle.P2Z:
+        w = W.make_p2z(100_000, seed=123)
+        comps = [0, 1, 3, 4, 5]
+    else:
+        w = W.make_p2r(10, 10_000, seed=123)
+        comps = [0, 1, 2, 3, 4, 5]
+    st, cv, stat, chi2 = oracle.step_batch(kind, w.state.T, w.cov.T, w.charge, w.hit.T,
+                                           w.hitcov.T, w.surf, w.bz, threads=4)
+    ok = (stat == 0) & w.reached
+    assert ok.mean() > 0.99
+    assert abs(chi2[ok].mean() - 2.0) < 0.03
+    truth = w.truth_surface.T[ok]
+    if kind == oracle.P2R:
+        # On the cylinder the free position coordinate is the tangential one
+        # (x, y alone mix in the radial direction, which has no variance).
+        u = np.stack([-np.sin(np.arctan2(st[ok, 1], st[ok, 0])),
+                      np.cos(np.arctan2(st[ok, 1], st[ok, 0]))], axis=1)
+        dt = np.einsum("ni,ni->n", u, st[ok, :2] - truth[:, :2])
+        Cxx = cv[ok, W.tri_index(0, 0)]
+        Cxy = cv[ok, W.tri_index(1, 0)]
+        Cyy = cv[ok, W.tri_index(1, 1)]
+        var_t = u[:, 0] ** 2 * Cxx + 2 * u[:, 0] * u[:, 1] * Cxy + u[:, 1] ** 2 * Cyy
+        pull = dt / np.sqrt(var_t)
+        assert abs(pull.mean()) < 0.02 and abs(pull.std() - 1.0) < 0.02, (pull.mean(), pull.std())
+        comps = [2, 3, 4, 5]
+    for c in comps:
+        d = st[ok, c] - truth[:, c]
+        if c == 4:
+            d = angle_diff(st[ok, c], truth[:, c])
+        pull = d / np.sqrt(cv[ok, W.tri_index(c, c)])
+        assert abs(pull.mean()) < 0.02, (c, pull.mean())
+        assert abs(pull.std() - 1.0) < 0.02, (c, pull.std())
+
+
+# --------------------------------------------------------- status bits
+
+def test_status_no_intersection_cases():
+    # p2r: a helix of diameter below R never reaches the cylinder.
+    k = 1.0 / (KAPPA_UNIT * BZ * 10.0)  # rho = 10 cm
+    p = np.array([0.0, 0.0, 0.0, k, 0.4, 1.0])
+    po, J, st = oracle.propagate_to_r(p, 1, BZ, 30.0)
+    assert st == oracle.NO_INTERSECT and np.all(po == p) and np.all(J == np.eye(6))
+    # p2r: start outside the cylinder
+    p2 = np.array([40.0, 0.0, 0.0, 0.1, 0.0, 1.0])
+    assert oracle.propagate_to_r(p2, 1, BZ, 30.0)[2] == oracle.NO_INTERSECT
+    # p2z: parallel to the plane (|cos theta| <= 1e-4), and just outside that band
+    for dth, exp in [(0.0, oracle.NO_INTERSECT), (5e-5, oracle.NO_INTERSECT),
+                     (-5e-5, oracle.NO_INTERSECT), (2e-4, 0)]:
+        p3 = np.array([0.0, 0.0, 0.0, 0.1, 0.0, math.pi / 2 + dth])
+        po3, _, st3 = oracle.propagate_to_z(p3, 1, BZ, 0.001)
+        assert st3 == exp
+        if exp:
+            assert np.all(po3 == p3)
+    # the full step leaves the input untouched
+    C = pack(random_spd(np.random.default_rng(1), SCALE))
+    pf, cf, _, stf = oracle.step(oracle.P2R, p, C, 1, [30, 0, 0], [1e-4, 0, 1e-4, 0, 0, 1e-4],
+                                 BZ, 30.0)
+    assert stf == oracle.NO_INTERSECT and np.all(pf == p) and np.all(cf == C)
+
+
+def test_status_s_not_pd_and_bad_k():
+    rng = np.random.default_rng(2)
+    C = random_spd(rng, SCALE)
+    p = np.array([20.0, 1.0, 30.0, 0.5, 0.3, 1.1])
+    H = np.zeros((2, 6))
+    H[0, 0] = H[1, 1] = 1.0
+    po, co, _, st = oracle.kalman_update(p, pack(C), H.ravel(), [-1.0, 0.0, 1e-4], [0.01, 0.0])
+    assert st == oracle.S_NOT_PD and np.all(po == p) and np.all(co == pack(C))
+    # strong x-k correlation and a large residual drive 1/pT negative
+    C2 = np.diag(SCALE ** 2)
+    C2[0, 3] = C2[3, 0] = 0.9 * SCALE[0] * SCALE[3]
+    po2, _, _, st2 = oracle.kalman_update(p, pack(C2), H.ravel(), [1e-6, 0.0, 1e-6], [-2000.0, 0])
+    assert st2 == oracle.BAD_K and po2[3] <= 0
+
+
+def test_batch_equals_single_track_calls():
+    w = W.make_p2z(64, seed=4)
+    st, cv, stat, chi2 = oracle.step_batch(oracle.P2Z, w.state.T, w.cov.T, w.charge, w.hit.T,
+                                           w.hitcov.T, w.surf, w.bz, threads=3)
+    for i in range(0, 64, 7):
+        po, co, c2, s = oracle.step(oracle.P2Z, w.state[:, i], w.cov[:, i], int(w.charge[i]),
+                                    w.hit[:, i], w.hitcov[:, i], w.bz, w.surf)
+        assert np.all(po == st[i]) and np.all(co == cv[i]) and s == stat[i]
