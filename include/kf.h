@@ -1,0 +1,196 @@
+/*
+ * kf.h -- C ABI of the GB300 batched Kalman-step library (libkf.so).
+ *
+ * What it computes (paper section 2, "The p2r and p2z program"): for every
+ * track of a batch, propagate the helix state and its covariance to a
+ * detector surface -- a plane at fixed z (propagateToZ, "p2z") or a cylinder
+ * at fixed r (propagateToR, "p2r") -- then Kalman-update the propagated track
+ * against the track's hit on that surface (KalmanUpdate).  The paper gives no
+ * formulas; the operations are the exact helix motion in a uniform field
+ * B = (0, 0, bz), the transport Jacobian J and C' = J C J^T, and the textbook
+ * linear Kalman update with a two-dimensional measurement:
+ *   p2z: m = (x, y) of the hit, H = [e_x; e_y], V = top-left 2x2 of the hit
+ *        covariance;
+ *   p2r: m = (r*phi, z) at the hit, i.e. residual (u . (hit - x'), z_hit - z')
+ *        with u = (-sin phi_h, cos phi_h), phi_h the azimuth of the hit, and
+ *        V = P V_hit P^T, P = [[-sin phi_h, cos phi_h, 0], [0, 0, 1]].
+ *
+ * Units and conventions.  State p = (x, y, z, k, phi, theta): cm, cm, cm,
+ * k = 1/pT in 1/GeV (k > 0), azimuth of the momentum in rad wrapped to
+ * (-pi, pi], polar angle in rad.  Charge q = +1/-1 (int8) is separate.  The
+ * signed curvature is omega = -q * 0.299792458e-2 * bz * k [1/cm] (a positive
+ * charge turns clockwise seen from +z).  Symmetric 6x6 covariances are packed
+ * lower-triangular, 21 floats in the order 00,10,11,20,21,22,30,...,55; the
+ * 3x3 hit covariance is packed the same way, 6 floats (xx,xy,yy,xz,yz,zz).
+ * p2r takes the first outward crossing of a track that starts strictly
+ * inside the cylinder; p2z allows negative path (a plane behind the track).
+ *
+ * Layouts (paper section 2: an array of MPTRK blocks, each a structure of
+ * arrays of bsize tracks).  Every per-track float array with C components
+ * is either
+ *   KF_SOA:   [C][n]            element (c, i) at c*n + i
+ *   KF_AOSOA: [ceil(n/W)][C][W] element (c, i) at (i/W)*C*W + c*W + i%W,
+ *             W = layout.width in {16, 32, 64, 128}; the last block is
+ *             padded (allocate ceil(n/W)*W*C floats; padding is never read
+ *             into a result and never written).
+ * The components are: state 6, covariance 21, hit 3, hit covariance 6.
+ * charge [n] and status [n] are plain arrays in both layouts; per-track
+ * surfaces are a plain [n] float array.
+ *
+ * Ownership and execution.  Every data pointer is a DEVICE pointer owned by
+ * the caller (allocated e.g. by PyTorch); the library allocates nothing per
+ * call and keeps no reference after the call returns.  Calls are enqueued on
+ * `stream` (a cudaStream_t; NULL = the legacy default stream) and return
+ * without synchronising.  Input and output may alias exactly (in place:
+ * state_in == state_out and/or cov_in == cov_out); any other overlap is
+ * undefined.  Float arrays must be 16-byte aligned.
+ *
+ * Errors.  Functions return KF_OK (0) or an error code; nothing is launched
+ * when an argument is rejected.  KF_ERR_CUDA carries the CUDA message,
+ * available from kf_last_error_string() (per calling thread).  Per-track
+ * numerical problems never fail a call: they set bits in status[i]
+ * (status may be NULL) and leave that track as described for each bit.
+ */
+#ifndef KF_H
+#define KF_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ------------------------------------------------------------ return codes */
+#define KF_OK              0
+#define KF_ERR_ARG         1  /* null/misaligned pointer, n < 0, bad layout  */
+#define KF_ERR_CUDA        2  /* a CUDA call or launch failed                */
+#define KF_ERR_UNSUPPORTED 3  /* valid but not provided (e.g. a variant)     */
+#define KF_ERR_TIMEOUT     4  /* a bounded device wait gave up               */
+
+/* ------------------------------------------------------- per-track status */
+#define KF_NO_INTERSECT 1u /* surface not reached: track copied unchanged    */
+#define KF_S_NOT_PD     2u /* H C' H^T + V not positive definite: the track
+                              is propagated but not updated                  */
+#define KF_BAD_K        4u /* updated 1/pT <= 0 (kept as computed)           */
+#define KF_NONFINITE    8u /* a non-finite value in the written result       */
+
+/* ---------------------------------------------------------------- layouts */
+#define KF_SOA   0
+#define KF_AOSOA 1
+
+typedef struct {
+    int32_t kind;  /* KF_SOA or KF_AOSOA                                  */
+    int32_t width; /* AoSoA block width W (16, 32, 64, 128); ignored for SoA */
+    int64_t n;     /* number of tracks (>= 0; 0 launches nothing)         */
+} kf_layout;
+
+/* ------------------------------------------------------- update variants */
+#define KF_FP32           0 /* all arithmetic in FP32                       */
+#define KF_FP64_UPDATE    1 /* FP32 propagation; S^-1, K and C'' in FP64     */
+#define KF_JOSEPH         2 /* FP32, Joseph-form C'' = (I-KH)C'(I-KH)^T+KVK^T */
+
+typedef struct {
+    float    bz;        /* field along +z in tesla                          */
+    int32_t  precision; /* KF_FP32, KF_FP64_UPDATE or KF_JOSEPH             */
+    uint32_t flags;     /* reserved, must be 0                              */
+} kf_params;
+
+/*
+ * kf_p2z_propagate_update -- one p2z step for n tracks (paper section 2:
+ * propagateToZ followed by KalmanUpdate).
+ *   params          field and update variant (host pointer, read in call)
+ *   layout          layout of every per-track float array (see above)
+ *   state_in/out    [6 comps] track states in / out
+ *   cov_in/out      [21 comps] packed covariances in / out
+ *   charge          [n] int8, +1 or -1
+ *   hit             [3 comps] hit position (x, y, z); z is not measured
+ *   hit_cov         [6 comps] packed 3x3 hit covariance (xx, xy, yy used)
+ *   z_surf          plane position(s): z_surf[0] for every track when
+ *                   surf_per_track == 0, else z_surf[i] (plain [n] array)
+ *   status          [n] uint8 per-track status bits, or NULL
+ *   stream          cudaStream_t
+ * A track with |cos(theta)| <= 1e-4 is treated as parallel to the plane
+ * (KF_NO_INTERSECT).
+ */
+int kf_p2z_propagate_update(const kf_params *params, kf_layout layout,
+                            const float *state_in, const float *cov_in,
+                            float *state_out, float *cov_out,
+                            const int8_t *charge, const float *hit,
+                            const float *hit_cov, const float *z_surf,
+                            int32_t surf_per_track, uint8_t *status,
+                            void *stream);
+
+/*
+ * kf_p2r_propagate_update -- one p2r step for n tracks (paper section 2:
+ * propagateToR followed by KalmanUpdate).  Arguments as for p2z, with
+ * r_surf the cylinder radius (or radii).  All six hit-covariance entries
+ * are used (V = P V_hit P^T).  A track that starts on or outside the
+ * cylinder, or whose helix stays inside it, gets KF_NO_INTERSECT.
+ */
+int kf_p2r_propagate_update(const kf_params *params, kf_layout layout,
+                            const float *state_in, const float *cov_in,
+                            float *state_out, float *cov_out,
+                            const int8_t *charge, const float *hit,
+                            const float *hit_cov, const float *r_surf,
+                            int32_t surf_per_track, uint8_t *status,
+                            void *stream);
+
+/*
+ * kf_p2z_propagate_update_host / kf_p2r_propagate_update_host -- the same
+ * steps on HOST arrays, the host<->device copies included (the paper's p2z
+ * throughput counts the transfers: section 4, Figure 6).
+ *   state_in ... status   HOST pointers with the layouts and sizes of the
+ *                         device call (AoSoA arrays padded to whole blocks;
+ *                         the padding of the output arrays may be
+ *                         overwritten).  Page-locked (pinned) memory lets
+ *                         the copies run asynchronously; pageable memory
+ *                         works but the driver stages it.  surf is a host
+ *                         scalar (surf_per_track == 0) or host [n] array.
+ *   workspace             DEVICE buffer owned by the caller, 256-byte
+ *                         aligned, of at least
+ *                         kf_host_workspace_bytes(layout, chunk_tracks) bytes
+ *   chunk_tracks          tracks per pipeline chunk (rounded up to the AoSoA
+ *                         width); 0 selects 262144
+ *   stream                the work starts after what is already queued on
+ *                         `stream`, and work queued on `stream` afterwards
+ *                         starts after it: synchronise `stream` before
+ *                         reading the host outputs.
+ * The batch is processed in chunks alternating between two streams the
+ * library creates once per device (kept until exit); while one chunk runs
+ * its kernel and copies out, the next copies in.  Calls on one device are
+ * serialised by a lock while they enqueue.  Errors as for the device calls;
+ * host pointers are not range-checked (their sizes are the caller's duty).
+ */
+int kf_p2z_propagate_update_host(const kf_params *params, kf_layout layout,
+                                 const float *state_in, const float *cov_in,
+                                 float *state_out, float *cov_out,
+                                 const int8_t *charge, const float *hit,
+                                 const float *hit_cov, const float *z_surf,
+                                 int32_t surf_per_track, uint8_t *status,
+                                 void *workspace, int64_t workspace_bytes,
+                                 int64_t chunk_tracks, void *stream);
+
+int kf_p2r_propagate_update_host(const kf_params *params, kf_layout layout,
+                                 const float *state_in, const float *cov_in,
+                                 float *state_out, float *cov_out,
+                                 const int8_t *charge, const float *hit,
+                                 const float *hit_cov, const float *r_surf,
+                                 int32_t surf_per_track, uint8_t *status,
+                                 void *workspace, int64_t workspace_bytes,
+                                 int64_t chunk_tracks, void *stream);
+
+/* Device workspace bytes the host-array calls need for `layout` and
+ * `chunk_tracks` (0 = default chunk); -1 for an invalid layout. */
+int64_t kf_host_workspace_bytes(kf_layout layout, int64_t chunk_tracks);
+
+/* Library version as MAJOR*10000 + MINOR*100 + PATCH. */
+int kf_version(void);
+
+/* Message of the last KF_ERR_* returned on the calling thread ("" if none). */
+const char *kf_last_error_string(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* KF_H */

@@ -1,0 +1,76 @@
+"""Error metrics between a CUDA result and the FP64 oracle (test infrastructure).
+
+Track parameters: |g - o| / max(|o|, floor) per component, with floors
+(1 cm, 1 cm, 1 cm, 1e-3 1/GeV, 1e-2 rad, 1e-2 rad) so that values near zero
+are judged on an absolute scale; phi is compared as an angular difference.
+Covariance: |g - o| / sqrt(o_ii o_jj), i.e. relative to the correlation
+scale of the pair, so that near-zero off-diagonal entries are not judged
+relative to themselves; where o_ii o_jj = 0 (the z row after a p2z step)
+the entry must be exactly zero.  Bounds: 1e-4 on parameters, 1e-3 on
+covariance elements.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+PARAM_FLOORS = np.array([1.0, 1.0, 1.0, 1e-3, 1e-2, 1e-2])
+TOL_PARAM = 1e-4
+TOL_COV = 1e-3
+_TRI = [(i, j) for i in range(6) for j in range(i + 1)]
+_DIAG = [i * (i + 1) // 2 + i for i in range(6)]
+
+
+def param_errors(g: np.ndarray, o: np.ndarray) -> np.ndarray:
+    """g, o: [n, 6] -> relative errors [n, 6]."""
+    g = np.asarray(g, dtype=np.float64)
+    o = np.asarray(o, dtype=np.float64)
+    d = np.abs(g - o)
+    d[:, 4] = np.abs((g[:, 4] - o[:, 4] + math.pi) % (2 * math.pi) - math.pi)
+    return d / np.maximum(np.abs(o), PARAM_FLOORS)
+
+
+def cov_errors(g: np.ndarray, o: np.ndarray) -> np.ndarray:
+    """g, o: [n, 21] packed -> errors relative to sqrt(o_ii o_jj), [n, 21]."""
+    g = np.asarray(g, dtype=np.float64)
+    o = np.asarray(o, dtype=np.float64)
+    diag = o[:, _DIAG]
+    scale = np.stack([np.sqrt(np.abs(diag[:, i] * diag[:, j])) for i, j in _TRI], axis=1)
+    d = np.abs(g - o)
+    with np.errstate(divide="ignore", invalid="ignore"):
+        err = np.where(scale > 0, d / np.where(scale > 0, scale, 1.0), np.where(d == 0, 0.0, np.inf))
+    return err
+
+
+def summary(err: np.ndarray) -> dict:
+    if err.size == 0:
+        return {"max": 0.0, "p99": 0.0, "mean": 0.0}
+    flat = err.reshape(-1)
+    return {"max": float(flat.max()), "p99": float(np.percentile(flat, 99)),
+            "mean": float(flat.mean())}
+
+
+def compare(g_state, g_cov, g_status, o_state, o_cov, o_status,
+            tol_param: float = TOL_PARAM, tol_cov: float = TOL_COV) -> dict:
+    """All arrays per track ([n, 6], [n, 21], [n]).  Returns a report dict with
+    'ok', error summaries per component and the status agreement."""
+    g_status = np.asarray(g_status).astype(np.int64)
+    o_status = np.asarray(o_status).astype(np.int64)
+    pe = param_errors(g_state, o_state)
+    ce = cov_errors(g_cov, o_cov)
+    status_equal = bool(np.array_equal(g_status, o_status))
+    rep = {
+        "n": int(len(o_status)),
+        "status_equal": status_equal,
+        "status_mismatch": int(np.sum(g_status != o_status)),
+        "flagged": int(np.sum(o_status != 0)),
+        "param": summary(pe),
+        "param_by_component": [summary(pe[:, c]) for c in range(6)],
+        "cov": summary(ce),
+        "tol_param": tol_param,
+        "tol_cov": tol_cov,
+    }
+    rep["ok"] = bool(status_equal and rep["param"]["max"] <= tol_param
+                     and rep["cov"]["max"] <= tol_cov)
+    return rep

@@ -1,0 +1,232 @@
+// kf_host.cu -- the single step on HOST arrays, with the host<->device
+// copies inside the call (the paper's p2z measurement includes the data
+// transfers; section 4, Figure 6 shows them on one stream before and after
+// the kernel).
+//
+// GB300 design: instead of one stream doing copy-in, kernel, copy-out in
+// sequence, the batch is cut into chunks that alternate between two
+// library-owned streams.  While chunk c runs its kernel and copies its
+// results out, chunk c+1 is already copying in on the other stream, so
+// both copy directions and the kernels overlap.  The device buffers for the
+// two chunks in flight live in a caller-provided workspace.
+#include <cstring>
+#include <mutex>
+
+#include <cuda_runtime.h>
+
+#include "kf_common.cuh"
+#include "kf_device.cuh"
+#include "kf_step.cuh"
+
+namespace kf {
+namespace {
+
+constexpr int kMaxDevices = 64;
+constexpr int64_t kDefaultChunk = 1 << 18;
+
+struct HostPipe {
+  cudaStream_t s[2];
+  cudaEvent_t fork;
+  cudaEvent_t join[2];
+};
+
+std::mutex g_pipe_mu;
+HostPipe *g_pipes[kMaxDevices] = {};
+
+// Two non-blocking streams and three events per device, created on first use
+// and kept for the life of the process.
+int get_pipe(HostPipe **out) {
+  int dev = 0;
+  if (int rc = check_cuda(cudaGetDevice(&dev), "cudaGetDevice")) return rc;
+  if (dev < 0 || dev >= kMaxDevices) return set_error(KF_ERR_UNSUPPORTED, "device %d", dev);
+  if (!g_pipes[dev]) {
+    HostPipe *p = new HostPipe;
+    for (int i = 0; i < 2; ++i) {
+      if (int rc = check_cuda(cudaStreamCreateWithFlags(&p->s[i], cudaStreamNonBlocking),
+                              "cudaStreamCreate"))
+        return rc;
+      if (int rc = check_cuda(cudaEventCreateWithFlags(&p->join[i], cudaEventDisableTiming),
+                              "cudaEventCreate"))
+        return rc;
+    }
+    if (int rc = check_cuda(cudaEventCreateWithFlags(&p->fork, cudaEventDisableTiming),
+                            "cudaEventCreate"))
+      return rc;
+    g_pipes[dev] = p;
+  }
+  *out = g_pipes[dev];
+  return KF_OK;
+}
+
+int64_t round256(int64_t x) { return (x + 255) & ~int64_t(255); }
+
+// Device buffers of one pipeline slot holding `chunk` tracks.
+struct Slot {
+  int64_t state_in, cov_in, hit, hitcov, state_out, cov_out, charge, status, surf, bytes;
+};
+
+Slot slot_layout(int64_t chunk) {
+  Slot s;
+  int64_t off = 0;
+  auto take = [&](int64_t b) {
+    const int64_t o = off;
+    off += round256(b);
+    return o;
+  };
+  s.state_in = take(4 * 6 * chunk);
+  s.cov_in = take(4 * 21 * chunk);
+  s.hit = take(4 * 3 * chunk);
+  s.hitcov = take(4 * 6 * chunk);
+  s.state_out = take(4 * 6 * chunk);
+  s.cov_out = take(4 * 21 * chunk);
+  s.charge = take(chunk);
+  s.status = take(chunk);
+  s.surf = take(4 * chunk);
+  s.bytes = off;
+  return s;
+}
+
+int64_t effective_chunk(const LayoutDesc &d, int64_t chunk_tracks) {
+  const int64_t W = d.soa ? 1 : (int64_t(1) << d.lw);
+  int64_t c = chunk_tracks > 0 ? chunk_tracks : kDefaultChunk;
+  c = ((c + W - 1) / W) * W;
+  const int64_t n_pad = ((d.n + W - 1) / W) * W;
+  return c < n_pad ? c : (n_pad > 0 ? n_pad : W);
+}
+
+// Copy tracks [c0, c0 + m) of a C-component array between the full host
+// array (n tracks) and a chunk buffer laid out for m tracks.
+cudaError_t copy_chunk(void *dst, const void *src, int C, const LayoutDesc &d, int64_t c0,
+                       int64_t m, bool to_device, cudaStream_t s) {
+  if (d.soa) {
+    if (to_device)
+      return cudaMemcpy2DAsync(dst, 4 * m, static_cast<const float *>(src) + c0, 4 * d.n, 4 * m,
+                               C, cudaMemcpyDefault, s);
+    return cudaMemcpy2DAsync(static_cast<float *>(dst) + c0, 4 * d.n, src, 4 * m, 4 * m, C,
+                             cudaMemcpyDefault, s);
+  }
+  const int64_t W = int64_t(1) << d.lw;
+  const int64_t blocks = (m + W - 1) / W;
+  const int64_t first = (c0 / W) * C * W;
+  const size_t bytes = 4 * blocks * C * W;
+  if (to_device)
+    return cudaMemcpyAsync(dst, static_cast<const float *>(src) + first, bytes, cudaMemcpyDefault,
+                           s);
+  return cudaMemcpyAsync(static_cast<float *>(dst) + first, src, bytes, cudaMemcpyDefault, s);
+}
+
+int run_host(int kind, const kf_params *params, kf_layout layout, const float *state_in,
+             const float *cov_in, float *state_out, float *cov_out, const int8_t *charge,
+             const float *hit, const float *hit_cov, const float *surf, int32_t surf_per_track,
+             uint8_t *status, void *workspace, int64_t workspace_bytes, int64_t chunk_tracks,
+             void *stream) {
+  clear_error();
+  if (!params) return set_error(KF_ERR_ARG, "params is NULL");
+  if (params->flags != 0) return set_error(KF_ERR_ARG, "params->flags must be 0");
+  if (params->precision < KF_FP32 || params->precision > KF_JOSEPH)
+    return set_error(KF_ERR_ARG, "unknown precision %d", params->precision);
+  LayoutDesc d;
+  if (int rc = check_layout(layout, &d)) return rc;
+  if (d.n == 0) return KF_OK;
+  if (!state_in || !cov_in || !state_out || !cov_out || !charge || !hit || !hit_cov || !surf)
+    return set_error(KF_ERR_ARG, "a required pointer is NULL");
+  if (surf_per_track != 0 && surf_per_track != 1)
+    return set_error(KF_ERR_ARG, "surf_per_track must be 0 or 1");
+  if (chunk_tracks < 0) return set_error(KF_ERR_ARG, "chunk_tracks < 0");
+  const int64_t chunk = effective_chunk(d, chunk_tracks);
+  const Slot sl = slot_layout(chunk);
+  if (workspace_bytes < 2 * sl.bytes)
+    return set_error(KF_ERR_ARG, "workspace holds %lld bytes, needs %lld",
+                     (long long)workspace_bytes, (long long)(2 * sl.bytes));
+  if (reinterpret_cast<uintptr_t>(workspace) & 255u)
+    return set_error(KF_ERR_ARG, "workspace must be 256-byte aligned");
+  if (int rc = check_device_range(workspace, 2 * sl.bytes, "workspace")) return rc;
+
+  std::lock_guard<std::mutex> lock(g_pipe_mu);
+  HostPipe *pipe = nullptr;
+  if (int rc = get_pipe(&pipe)) return rc;
+  cudaStream_t caller = static_cast<cudaStream_t>(stream);
+  if (int rc = check_cuda(cudaEventRecord(pipe->fork, caller), "cudaEventRecord")) return rc;
+  for (int i = 0; i < 2; ++i)
+    if (int rc = check_cuda(cudaStreamWaitEvent(pipe->s[i], pipe->fork, 0), "cudaStreamWaitEvent"))
+      return rc;
+
+  char *ws = static_cast<char *>(workspace);
+  int64_t c = 0;
+  for (int64_t c0 = 0; c0 < d.n; c0 += chunk, ++c) {
+    const int64_t m = (d.n - c0 < chunk) ? d.n - c0 : chunk;
+    cudaStream_t s = pipe->s[c & 1];
+    char *base = ws + (c & 1) * sl.bytes;
+    float *d_st_in = reinterpret_cast<float *>(base + sl.state_in);
+    float *d_cv_in = reinterpret_cast<float *>(base + sl.cov_in);
+    float *d_hit = reinterpret_cast<float *>(base + sl.hit);
+    float *d_hc = reinterpret_cast<float *>(base + sl.hitcov);
+    float *d_st_out = reinterpret_cast<float *>(base + sl.state_out);
+    float *d_cv_out = reinterpret_cast<float *>(base + sl.cov_out);
+    int8_t *d_q = reinterpret_cast<int8_t *>(base + sl.charge);
+    uint8_t *d_status = reinterpret_cast<uint8_t *>(base + sl.status);
+    float *d_surf = reinterpret_cast<float *>(base + sl.surf);
+    LayoutDesc dc = d;
+    dc.n = m;
+    cudaError_t e = cudaSuccess;
+    if (e == cudaSuccess) e = copy_chunk(d_st_in, state_in, 6, d, c0, m, true, s);
+    if (e == cudaSuccess) e = copy_chunk(d_cv_in, cov_in, 21, d, c0, m, true, s);
+    if (e == cudaSuccess) e = copy_chunk(d_hit, hit, 3, d, c0, m, true, s);
+    if (e == cudaSuccess) e = copy_chunk(d_hc, hit_cov, 6, d, c0, m, true, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d_q, charge + c0, m, cudaMemcpyDefault, s);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(d_surf, surf_per_track ? surf + c0 : surf,
+                          surf_per_track ? 4 * m : 4, cudaMemcpyDefault, s);
+    if (int rc = check_cuda(e, "host-to-device copy")) return rc;
+    StepArgs a{d_st_in, d_cv_in, d_st_out, d_cv_out, d_q,  d_hit, d_hc, d_surf,
+               status ? d_status : nullptr, m, dc.soa, dc.lw, params->bz, surf_per_track};
+    if (int rc = launch_step_kernel(kind, params->precision, a, s)) return rc;
+    e = copy_chunk(state_out, d_st_out, 6, d, c0, m, false, s);
+    if (e == cudaSuccess) e = copy_chunk(cov_out, d_cv_out, 21, d, c0, m, false, s);
+    if (e == cudaSuccess && status)
+      e = cudaMemcpyAsync(status + c0, d_status, m, cudaMemcpyDefault, s);
+    if (int rc = check_cuda(e, "device-to-host copy")) return rc;
+  }
+  for (int i = 0; i < 2; ++i) {
+    if (int rc = check_cuda(cudaEventRecord(pipe->join[i], pipe->s[i]), "cudaEventRecord"))
+      return rc;
+    if (int rc = check_cuda(cudaStreamWaitEvent(caller, pipe->join[i], 0), "cudaStreamWaitEvent"))
+      return rc;
+  }
+  return KF_OK;
+}
+
+}  // namespace
+}  // namespace kf
+
+extern "C" int64_t kf_host_workspace_bytes(kf_layout layout, int64_t chunk_tracks) {
+  kf::LayoutDesc d;
+  if (kf::check_layout(layout, &d) || chunk_tracks < 0) return -1;
+  return 2 * kf::slot_layout(kf::effective_chunk(d, chunk_tracks)).bytes;
+}
+
+extern "C" int kf_p2z_propagate_update_host(const kf_params *params, kf_layout layout,
+                                            const float *state_in, const float *cov_in,
+                                            float *state_out, float *cov_out,
+                                            const int8_t *charge, const float *hit,
+                                            const float *hit_cov, const float *z_surf,
+                                            int32_t surf_per_track, uint8_t *status,
+                                            void *workspace, int64_t workspace_bytes,
+                                            int64_t chunk_tracks, void *stream) {
+  return kf::run_host(kf::kP2z, params, layout, state_in, cov_in, state_out, cov_out, charge, hit,
+                      hit_cov, z_surf, surf_per_track, status, workspace, workspace_bytes,
+                      chunk_tracks, stream);
+}
+
+extern "C" int kf_p2r_propagate_update_host(const kf_params *params, kf_layout layout,
+                                            const float *state_in, const float *cov_in,
+                                            float *state_out, float *cov_out,
+                                            const int8_t *charge, const float *hit,
+                                            const float *hit_cov, const float *r_surf,
+                                            int32_t surf_per_track, uint8_t *status,
+                                            void *workspace, int64_t workspace_bytes,
+                                            int64_t chunk_tracks, void *stream) {
+  return kf::run_host(kf::kP2r, params, layout, state_in, cov_in, state_out, cov_out, charge, hit,
+                      hit_cov, r_surf, surf_per_track, status, workspace, workspace_bytes,
+                      chunk_tracks, stream);
+}

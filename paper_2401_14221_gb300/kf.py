@@ -1,0 +1,346 @@
+"""Python binding of libkf.so: the C-ABI entry points under the same names.
+
+Argument marshalling only -- every step of the Kalman path runs in the CUDA
+kernels of libkf.so.  Tensors are passed as raw device pointers; PyTorch is
+used for device memory and streams.  If the library is not built, or a
+tensor is not on a CUDA device, the calls raise: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import dataclasses
+import os
+import re
+from typing import Optional
+
+import numpy as np
+import torch
+
+from . import workload as W
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "_build", "libkf.so")
+HEADER = os.path.join(os.path.dirname(_PKG), "include", "kf.h")
+
+KF_OK, KF_ERR_ARG, KF_ERR_CUDA, KF_ERR_UNSUPPORTED, KF_ERR_TIMEOUT = 0, 1, 2, 3, 4
+NO_INTERSECT, S_NOT_PD, BAD_K, NONFINITE = 1, 2, 4, 8
+KF_SOA, KF_AOSOA = 0, 1
+KF_FP32, KF_FP64_UPDATE, KF_JOSEPH = 0, 1, 2
+
+
+class KfError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"libkf error {code}: {msg}")
+        self.code = code
+
+
+class kf_layout(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("width", ctypes.c_int32), ("n", ctypes.c_int64)]
+
+
+class kf_params(ctypes.Structure):
+    _fields_ = [("bz", ctypes.c_float), ("precision", ctypes.c_int32), ("flags", ctypes.c_uint32)]
+
+
+_lib = None
+_VP = ctypes.c_void_p
+
+
+def load():
+    """Load libkf.so (built in-tree by ``__graft_entry__.build()``)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"{LIB_PATH} is not built; run __graft_entry__.build() first")
+    lib = ctypes.CDLL(LIB_PATH)
+    step_args = [ctypes.POINTER(kf_params), kf_layout, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP,
+                 ctypes.c_int32, _VP, _VP]
+    for name in ("kf_p2z_propagate_update", "kf_p2r_propagate_update"):
+        fn = getattr(lib, name)
+        fn.argtypes = step_args
+        fn.restype = ctypes.c_int
+    host_args = step_args[:-1] + [_VP, ctypes.c_int64, ctypes.c_int64, _VP]
+    for name in ("kf_p2z_propagate_update_host", "kf_p2r_propagate_update_host"):
+        fn = getattr(lib, name)
+        fn.argtypes = host_args
+        fn.restype = ctypes.c_int
+    lib.kf_host_workspace_bytes.argtypes = [kf_layout, ctypes.c_int64]
+    lib.kf_host_workspace_bytes.restype = ctypes.c_int64
+    lib.kf_version.restype = ctypes.c_int
+    lib.kf_last_error_string.restype = ctypes.c_char_p
+    _lib = lib
+    return lib
+
+
+def header_functions(path: str = HEADER):
+    """Names of the functions declared in include/kf.h."""
+    text = open(path).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(kf_[a-z0-9_]+)\s*\(", text)))
+
+
+def _ptr(t, name: str, dtype: Optional[torch.dtype] = None):
+    if t is None:
+        return None
+    if isinstance(t, int):
+        return t
+    if not isinstance(t, torch.Tensor):
+        raise TypeError(f"{name}: expected a torch.Tensor or an int pointer")
+    if not t.is_cuda:
+        raise ValueError(f"{name}: tensor must be on a CUDA device")
+    if dtype is not None and t.dtype != dtype:
+        raise TypeError(f"{name}: expected {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name}: tensor must be contiguous")
+    return t.data_ptr()
+
+
+def _stream(stream):
+    if stream is None:
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, torch.cuda.Stream):
+        return stream.cuda_stream
+    return int(stream)
+
+
+def _check(rc: int):
+    if rc != KF_OK:
+        raise KfError(rc, load().kf_last_error_string().decode())
+
+
+def make_layout(kind: int, width: int, n: int) -> kf_layout:
+    return kf_layout(int(kind), int(width), int(n))
+
+
+def make_params(bz: float, precision: int = KF_FP32, flags: int = 0) -> kf_params:
+    return kf_params(float(bz), int(precision), int(flags))
+
+
+def _step(fn_name, params, layout, state_in, cov_in, state_out, cov_out, charge, hit, hit_cov,
+          surf, surf_per_track, status, stream):
+    lib = load()
+    f32, i8, u8 = torch.float32, torch.int8, torch.uint8
+    rc = getattr(lib, fn_name)(
+        ctypes.byref(params), layout,
+        _ptr(state_in, "state_in", f32), _ptr(cov_in, "cov_in", f32),
+        _ptr(state_out, "state_out", f32), _ptr(cov_out, "cov_out", f32),
+        _ptr(charge, "charge", i8), _ptr(hit, "hit", f32), _ptr(hit_cov, "hit_cov", f32),
+        _ptr(surf, "surf", f32), int(surf_per_track), _ptr(status, "status", u8),
+        _stream(stream))
+    _check(rc)
+
+
+def kf_p2z_propagate_update(params, layout, state_in, cov_in, state_out, cov_out, charge, hit,
+                            hit_cov, z_surf, surf_per_track=0, status=None, stream=None):
+    """C-ABI kf_p2z_propagate_update (include/kf.h); raises KfError on failure."""
+    _step("kf_p2z_propagate_update", params, layout, state_in, cov_in, state_out, cov_out,
+          charge, hit, hit_cov, z_surf, surf_per_track, status, stream)
+
+
+def kf_p2r_propagate_update(params, layout, state_in, cov_in, state_out, cov_out, charge, hit,
+                            hit_cov, r_surf, surf_per_track=0, status=None, stream=None):
+    """C-ABI kf_p2r_propagate_update (include/kf.h); raises KfError on failure."""
+    _step("kf_p2r_propagate_update", params, layout, state_in, cov_in, state_out, cov_out,
+          charge, hit, hit_cov, r_surf, surf_per_track, status, stream)
+
+
+def _host_ptr(t, name: str, dtype: torch.dtype):
+    if t is None:
+        return None
+    if isinstance(t, int):
+        return t
+    if t.is_cuda:
+        raise ValueError(f"{name}: the host-array call takes CPU tensors")
+    if t.dtype != dtype or not t.is_contiguous():
+        raise TypeError(f"{name}: expected a contiguous {dtype} tensor")
+    return t.data_ptr()
+
+
+def _step_host(fn_name, params, layout, state_in, cov_in, state_out, cov_out, charge, hit,
+               hit_cov, surf, surf_per_track, status, workspace, chunk_tracks, stream):
+    lib = load()
+    f32, i8, u8 = torch.float32, torch.int8, torch.uint8
+    ws = _ptr(workspace, "workspace")
+    ws_bytes = workspace.numel() * workspace.element_size() if isinstance(workspace, torch.Tensor) \
+        else int(1 << 62)
+    rc = getattr(lib, fn_name)(
+        ctypes.byref(params), layout,
+        _host_ptr(state_in, "state_in", f32), _host_ptr(cov_in, "cov_in", f32),
+        _host_ptr(state_out, "state_out", f32), _host_ptr(cov_out, "cov_out", f32),
+        _host_ptr(charge, "charge", i8), _host_ptr(hit, "hit", f32),
+        _host_ptr(hit_cov, "hit_cov", f32), _host_ptr(surf, "surf", f32), int(surf_per_track),
+        _host_ptr(status, "status", u8), ws, ws_bytes, int(chunk_tracks), _stream(stream))
+    _check(rc)
+
+
+def kf_p2z_propagate_update_host(params, layout, state_in, cov_in, state_out, cov_out, charge,
+                                 hit, hit_cov, z_surf, surf_per_track=0, status=None,
+                                 workspace=None, chunk_tracks=0, stream=None):
+    """C-ABI kf_p2z_propagate_update_host: host arrays in and out."""
+    _step_host("kf_p2z_propagate_update_host", params, layout, state_in, cov_in, state_out,
+               cov_out, charge, hit, hit_cov, z_surf, surf_per_track, status, workspace,
+               chunk_tracks, stream)
+
+
+def kf_p2r_propagate_update_host(params, layout, state_in, cov_in, state_out, cov_out, charge,
+                                 hit, hit_cov, r_surf, surf_per_track=0, status=None,
+                                 workspace=None, chunk_tracks=0, stream=None):
+    """C-ABI kf_p2r_propagate_update_host: host arrays in and out."""
+    _step_host("kf_p2r_propagate_update_host", params, layout, state_in, cov_in, state_out,
+               cov_out, charge, hit, hit_cov, r_surf, surf_per_track, status, workspace,
+               chunk_tracks, stream)
+
+
+def kf_host_workspace_bytes(layout, chunk_tracks: int = 0) -> int:
+    return int(load().kf_host_workspace_bytes(layout, int(chunk_tracks)))
+
+
+def kf_version() -> int:
+    return int(load().kf_version())
+
+
+def kf_last_error_string() -> str:
+    return load().kf_last_error_string().decode()
+
+
+# ------------------------------------------------------------ device batches
+
+@dataclasses.dataclass
+class DeviceBatch:
+    """One workload resident on the GPU in a given layout (plumbing only)."""
+    kind: int
+    n: int
+    layout: kf_layout
+    state_in: torch.Tensor
+    cov_in: torch.Tensor
+    state_out: torch.Tensor
+    cov_out: torch.Tensor
+    charge: torch.Tensor
+    hit: torch.Tensor
+    hit_cov: torch.Tensor
+    surf: torch.Tensor
+    status: torch.Tensor
+    bz: float
+
+    def run(self, precision: int = KF_FP32, stream=None, in_place: bool = False):
+        fn = kf_p2z_propagate_update if self.kind == W.P2Z else kf_p2r_propagate_update
+        so = self.state_in if in_place else self.state_out
+        co = self.cov_in if in_place else self.cov_out
+        fn(make_params(self.bz, precision), self.layout, self.state_in, self.cov_in, so, co,
+           self.charge, self.hit, self.hit_cov, self.surf, int(self.surf.numel() > 1),
+           self.status, stream)
+
+    def download(self):
+        """Results as SoA numpy arrays: (state [6,n], cov [21,n], status [n])."""
+        return (from_device(self.state_out, 6, self.n, self.layout),
+                from_device(self.cov_out, 21, self.n, self.layout),
+                self.status.cpu().numpy())
+
+    def nbytes(self) -> int:
+        return sum(t.numel() * t.element_size() for t in
+                   (self.state_in, self.cov_in, self.state_out, self.cov_out, self.charge,
+                    self.hit, self.hit_cov, self.surf, self.status))
+
+
+def to_device(a: np.ndarray, layout: kf_layout, device) -> torch.Tensor:
+    """[C, n] float32 SoA -> a flat device tensor in `layout`."""
+    a = np.ascontiguousarray(a, dtype=np.float32)
+    if layout.kind == KF_AOSOA:
+        a = W.to_aosoa(a, layout.width)
+    return torch.from_numpy(a.reshape(-1).copy()).to(device)
+
+
+def from_device(t: torch.Tensor, C: int, n: int, layout: kf_layout) -> np.ndarray:
+    a = t.cpu().numpy()
+    if layout.kind == KF_AOSOA:
+        nb = W.aosoa_blocks(n, layout.width)
+        return W.from_aosoa(a.reshape(nb, C, layout.width), n)
+    return a.reshape(C, n)
+
+
+def upload(w: W.Workload, layout_kind: int = KF_SOA, width: int = 32, device="cuda",
+           surf_per_track: Optional[np.ndarray] = None) -> DeviceBatch:
+    lay = make_layout(layout_kind, width, w.n)
+    st_in = to_device(w.state, lay, device)
+    cv_in = to_device(w.cov, lay, device)
+    surf = (torch.tensor([w.surf], dtype=torch.float32, device=device) if surf_per_track is None
+            else torch.from_numpy(np.ascontiguousarray(surf_per_track, dtype=np.float32)).to(device))
+    return DeviceBatch(
+        kind=w.kind, n=w.n, layout=lay, state_in=st_in, cov_in=cv_in,
+        state_out=torch.empty_like(st_in), cov_out=torch.empty_like(cv_in),
+        charge=torch.from_numpy(np.ascontiguousarray(w.charge)).to(device),
+        hit=to_device(w.hit, lay, device), hit_cov=to_device(w.hitcov, lay, device),
+        surf=surf, status=torch.zeros(w.n, dtype=torch.uint8, device=device), bz=w.bz)
+
+
+@dataclasses.dataclass
+class HostBatch:
+    """One workload in pinned host memory for the host-array calls."""
+    kind: int
+    n: int
+    layout: kf_layout
+    state_in: torch.Tensor
+    cov_in: torch.Tensor
+    state_out: torch.Tensor
+    cov_out: torch.Tensor
+    charge: torch.Tensor
+    hit: torch.Tensor
+    hit_cov: torch.Tensor
+    surf: torch.Tensor
+    status: torch.Tensor
+    workspace: torch.Tensor
+    bz: float
+    chunk_tracks: int = 0
+
+    def run(self, precision: int = KF_FP32, stream=None):
+        fn = kf_p2z_propagate_update_host if self.kind == W.P2Z else kf_p2r_propagate_update_host
+        fn(make_params(self.bz, precision), self.layout, self.state_in, self.cov_in,
+           self.state_out, self.cov_out, self.charge, self.hit, self.hit_cov, self.surf,
+           int(self.surf.numel() > 1), self.status, self.workspace, self.chunk_tracks, stream)
+
+    def h2d_bytes(self) -> int:
+        return sum(t.numel() * t.element_size() for t in
+                   (self.state_in, self.cov_in, self.charge, self.hit, self.hit_cov, self.surf))
+
+    def d2h_bytes(self) -> int:
+        return sum(t.numel() * t.element_size() for t in (self.state_out, self.cov_out,
+                                                          self.status))
+
+    def download(self):
+        lay = self.layout
+
+        def conv(t, C):
+            a = t.numpy()
+            if lay.kind == KF_AOSOA:
+                return W.from_aosoa(a.reshape(W.aosoa_blocks(self.n, lay.width), C, lay.width),
+                                    self.n)
+            return a.reshape(C, self.n)
+        return conv(self.state_out, 6), conv(self.cov_out, 21), self.status.numpy().copy()
+
+
+def host_upload(w: W.Workload, layout_kind: int = KF_SOA, width: int = 32, device="cuda",
+                chunk_tracks: int = 0, pinned: bool = True) -> HostBatch:
+    lay = make_layout(layout_kind, width, w.n)
+
+    def host(a):
+        a = np.ascontiguousarray(a, dtype=np.float32)
+        if lay.kind == KF_AOSOA:
+            a = W.to_aosoa(a, lay.width)
+        t = torch.from_numpy(a.reshape(-1).copy())
+        return t.pin_memory() if pinned else t
+
+    st_in, cv_in = host(w.state), host(w.cov)
+    st_out = torch.empty_like(st_in, pin_memory=pinned)
+    cv_out = torch.empty_like(cv_in, pin_memory=pinned)
+    q = torch.from_numpy(np.ascontiguousarray(w.charge))
+    status = torch.zeros(w.n, dtype=torch.uint8)
+    surf = torch.tensor([w.surf], dtype=torch.float32)
+    if pinned:
+        q, status = q.pin_memory(), status.pin_memory()
+    ws_bytes = kf_host_workspace_bytes(lay, chunk_tracks)
+    ws = torch.empty(ws_bytes, dtype=torch.uint8, device=device)
+    return HostBatch(kind=w.kind, n=w.n, layout=lay, state_in=st_in, cov_in=cv_in,
+                     state_out=st_out, cov_out=cv_out, charge=q, hit=host(w.hit),
+                     hit_cov=host(w.hitcov), surf=surf, status=status, workspace=ws, bz=w.bz,
+                     chunk_tracks=chunk_tracks)

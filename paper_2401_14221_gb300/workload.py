@@ -105,13 +105,15 @@ def simulate_to_z(truth: np.ndarray, q, bz: float, zt, steps: int = 64):
     return out, S
 
 
-def simulate_to_r(truth: np.ndarray, q, bz: float, R: float, h: float = 0.5,
-                  s_max: Optional[float] = None, bisect: int = 48):
+def simulate_to_r(truth: np.ndarray, q, bz: float, R: float, h: float = 1.0,
+                  s_max: Optional[float] = None, refine: int = 8):
     """True state at the first outward crossing of radius R (float64 [6, n]).
 
-    Fixed RK4 steps of size h until r >= R, then bisection on the size of the
-    last step.  Tracks that start outside the cylinder or do not reach it
-    within s_max (default 4R) are returned as NaN with reached = False."""
+    Fixed RK4 steps of size h until r >= R, then Newton iterations on the
+    length f of the last (partial) RK4 step, solving |P(f)|^2 = R^2 with the
+    direction returned by the same sub-step as derivative.  Tracks that start
+    outside the cylinder or do not reach it within s_max (default 4R) are
+    returned as NaN with reached = False."""
     x0, y0, z0, k, phi, th = [np.asarray(a, dtype=np.float64) for a in truth]
     n = x0.shape[0]
     if s_max is None:
@@ -136,16 +138,16 @@ def simulate_to_r(truth: np.ndarray, q, bz: float, R: float, h: float = 0.5,
         crossed = xn * xn + yn * yn >= R2
         if np.any(crossed):
             c = np.nonzero(crossed)[0]
-            lo = np.zeros(c.size)
-            hi = np.full(c.size, h)
-            for _b in range(bisect):
-                mid = 0.5 * (lo + hi)
-                xm, ym, _, _ = rk4_transverse(xa[c], ya[c], txa[c], tya[c], ka[c], mid, 1)
-                inside = xm * xm + ym * ym < R2
-                lo = np.where(inside, mid, lo)
-                hi = np.where(inside, hi, mid)
-            f = 0.5 * (lo + hi)
-            xf, yf, txf, tyf = rk4_transverse(xa[c], ya[c], txa[c], tya[c], ka[c], f, 1)
+            xc, yc, txc, tyc, kc = xa[c], ya[c], txa[c], tya[c], ka[c]
+            # start from the straight-line estimate inside the step
+            b = xc * txc + yc * tyc
+            f = np.clip(-b + np.sqrt(np.maximum(b * b - (xc * xc + yc * yc - R2), 0.0)), 0.0, h)
+            for _it in range(refine):
+                xf, yf, txf, tyf = rk4_transverse(xc, yc, txc, tyc, kc, f, 1)
+                g = xf * xf + yf * yf - R2
+                dg = 2.0 * (xf * txf + yf * tyf)
+                f = np.clip(f - g / dg, 0.0, h)
+            xf, yf, txf, tyf = rk4_transverse(xc, yc, txc, tyc, kc, f, 1)
             idx = active[c]
             out_x[idx], out_y[idx], out_tx[idx], out_ty[idx] = xf, yf, txf, tyf
             out_s[idx] = S[idx] + f
@@ -224,7 +226,7 @@ def _smear(rng, truth, C):
 
 def make_p2z(n: int, seed: int = 1, pt_range=(0.5, 10.0), eta_range=(1.5, 2.5),
              zt: float = 50.0, bz: float = 3.8, hit_sigma: float = 0.01,
-             rk4_steps: int = 64) -> Workload:
+             rk4_steps: int = 24) -> Workload:
     """p2z single step: forward tracks to the plane z = zt, hits smeared in x, y."""
     ss = np.random.SeedSequence(seed)
     r_trk, r_cov, r_smear, r_hit = [np.random.Generator(np.random.PCG64(s)) for s in ss.spawn(4)]
@@ -247,7 +249,7 @@ def make_p2z(n: int, seed: int = 1, pt_range=(0.5, 10.0), eta_range=(1.5, 2.5),
 
 def make_p2r(nevts: int, ntrks: int, seed: int = 1, pt_range=(0.5, 10.0),
              eta_range=(-1.5, 1.5), R: float = 30.0, bz: float = 3.8,
-             rphi_sigma: float = 0.01, z_sigma: float = 0.05, rk4_h: float = 0.5) -> Workload:
+             rphi_sigma: float = 0.01, z_sigma: float = 0.05, rk4_h: float = 1.0) -> Workload:
     """p2r single step: central tracks to the cylinder r = R; the hit sits on
     the cylinder, smeared along r*phi and z."""
     n = nevts * ntrks
@@ -295,3 +297,25 @@ def from_aosoa(b: np.ndarray, n: int) -> np.ndarray:
     """[nb, C, W] -> [C, n]."""
     nb, C, W = b.shape
     return np.ascontiguousarray(b.transpose(1, 0, 2).reshape(C, nb * W)[:, :n])
+
+
+# ------------------------------------------------------- named workloads
+
+def single_step_p2z(seed: int = 1) -> Workload:
+    """p2z single step: 8,192 forward tracks to z = 50 cm."""
+    return make_p2z(8192, seed=seed)
+
+
+def single_step_p2r_paper_scale(seed: int = 1) -> Workload:
+    """p2r at the paper's scale: 100 events x 9,600 tracks to r = 30 cm."""
+    return make_p2r(100, 9600, seed=seed)
+
+
+def precision_p2z(n: int = 1_000_000, seed: int = 3) -> Workload:
+    """Precision study, p2z half: pT extended to 0.2-100 GeV."""
+    return make_p2z(n, seed=seed, pt_range=(0.2, 100.0))
+
+
+def precision_p2r(n: int = 1_000_000, seed: int = 4) -> Workload:
+    """Precision study, p2r half: pT extended to 0.2-100 GeV."""
+    return make_p2r(100, n // 100, seed=seed, pt_range=(0.2, 100.0))

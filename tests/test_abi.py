@@ -1,0 +1,56 @@
+"""The C-ABI library builds, loads and exports what include/kf.h declares;
+argument checks that run before any CUDA call (no GPU needed)."""
+import ctypes
+
+import pytest
+
+from paper_2401_14221_gb300 import build as kbuild
+from paper_2401_14221_gb300 import kf
+
+
+@pytest.fixture(scope="module")
+def lib():
+    kbuild.build()
+    return kf.load()
+
+
+def test_exports_every_declared_function(lib):
+    names = kf.header_functions()
+    assert "kf_p2z_propagate_update" in names and "kf_p2r_propagate_update" in names
+    for name in names:
+        assert hasattr(lib, name), f"libkf.so does not export {name}"
+
+
+def test_version(lib):
+    assert kf.kf_version() == 100
+
+
+def _call(lib, name, params, layout):
+    fn = getattr(lib, name)
+    p = ctypes.byref(params) if params is not None else None
+    dummy = ctypes.c_void_p(16)  # never dereferenced: every case fails before use
+    return fn(p, layout, dummy, dummy, dummy, dummy, dummy, dummy, dummy, dummy, 0, None, None)
+
+
+@pytest.mark.parametrize("name", ["kf_p2z_propagate_update", "kf_p2r_propagate_update"])
+def test_argument_checks_without_gpu(lib, name):
+    good = kf.make_params(3.8)
+    assert _call(lib, name, None, kf.make_layout(kf.KF_SOA, 0, 10)) == kf.KF_ERR_ARG
+    assert "params" in kf.kf_last_error_string()
+    assert _call(lib, name, kf.make_params(3.8, flags=1), kf.make_layout(0, 0, 10)) == kf.KF_ERR_ARG
+    assert _call(lib, name, kf.make_params(3.8, precision=7), kf.make_layout(0, 0, 10)) == kf.KF_ERR_ARG
+    assert _call(lib, name, good, kf.make_layout(kf.KF_SOA, 0, -1)) == kf.KF_ERR_ARG
+    assert _call(lib, name, good, kf.make_layout(5, 0, 10)) == kf.KF_ERR_ARG
+    assert _call(lib, name, good, kf.make_layout(kf.KF_AOSOA, 24, 10)) == kf.KF_ERR_ARG
+    assert "width" in kf.kf_last_error_string()
+    # n = 0 launches nothing and succeeds, whatever the pointers
+    assert _call(lib, name, good, kf.make_layout(kf.KF_AOSOA, 64, 0)) == kf.KF_OK
+    assert kf.kf_last_error_string() == ""
+
+
+def test_binding_refuses_cpu_tensors(lib):
+    import torch
+    t = torch.zeros(6, dtype=torch.float32)
+    with pytest.raises(ValueError):
+        kf.kf_p2z_propagate_update(kf.make_params(3.8), kf.make_layout(0, 0, 1), t, t, t, t,
+                                   torch.zeros(1, dtype=torch.int8), t, t, t)

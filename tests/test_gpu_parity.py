@@ -1,0 +1,275 @@
+"""CUDA path vs the FP64 oracle, element by element, through the C ABI.
+
+Bounds (oracle/compare.py): relative error <= 1e-4 on track parameters
+(floors for values near zero, phi as an angle) and <= 1e-3 on covariance
+elements relative to sqrt(C_ii C_jj); per-track status bits must agree
+exactly.  Full-size workloads run whole on the GPU and are checked on a
+sample that always includes the first and last tracks (the ragged tail).
+"""
+import ctypes
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from oracle import compare
+from paper_2401_14221_gb300 import build as kbuild
+from paper_2401_14221_gb300 import kf
+from paper_2401_14221_gb300 import workload as W
+
+pytestmark = pytest.mark.gpu
+
+LAYOUTS = [(kf.KF_SOA, 0), (kf.KF_AOSOA, 16), (kf.KF_AOSOA, 32), (kf.KF_AOSOA, 64),
+           (kf.KF_AOSOA, 128)]
+VARIANT_FORM = {kf.KF_FP32: oracle.FORM_STANDARD, kf.KF_FP64_UPDATE: oracle.FORM_STANDARD,
+                kf.KF_JOSEPH: oracle.FORM_JOSEPH}
+
+
+@pytest.fixture(scope="module")
+def dev():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    kbuild.build()
+    torch.cuda.set_device(0)
+    return torch.device("cuda:0")
+
+
+@pytest.fixture(scope="module")
+def w_p2z():
+    return W.single_step_p2z()
+
+
+@pytest.fixture(scope="module")
+def w_p2r():
+    return W.single_step_p2r_paper_scale()
+
+
+@pytest.fixture(scope="module")
+def w_prec():
+    return W.precision_p2z(), W.precision_p2r()
+
+
+def sample_indices(n, k=20000):
+    if n <= k:
+        return np.arange(n)
+    idx = np.concatenate([np.arange(256), np.linspace(0, n - 1, k).astype(np.int64),
+                          np.arange(n - 256, n)])
+    return np.unique(idx)
+
+
+def oracle_on(w, idx, form=oracle.FORM_STANDARD, surf=None):
+    s = w.surf if surf is None else surf[idx]
+    return oracle.step_batch(w.kind, w.state.T[idx], w.cov.T[idx], w.charge[idx], w.hit.T[idx],
+                             w.hitcov.T[idx], s, w.bz, form, threads=8)
+
+
+def check(w, b, idx, form=oracle.FORM_STANDARD, surf=None):
+    st, cv, stat = b.download()
+    o_st, o_cv, o_stat, _ = oracle_on(w, idx, form, surf)
+    rep = compare.compare(st.T[idx], cv.T[idx], stat[idx], o_st, o_cv, o_stat)
+    assert rep["ok"], rep
+    return rep
+
+
+def run(w, dev, layout=(kf.KF_SOA, 0), precision=kf.KF_FP32, surf=None):
+    b = kf.upload(w, layout[0], layout[1], dev, surf)
+    b.run(precision)
+    torch.cuda.synchronize()
+    return b
+
+
+# ------------------------------------------------------------ workloads
+
+@pytest.mark.parametrize("layout", LAYOUTS)
+def test_p2z_single_step_8192(dev, w_p2z, layout):
+    b = run(w_p2z, dev, layout)
+    check(w_p2z, b, np.arange(w_p2z.n))
+
+
+@pytest.mark.parametrize("layout", LAYOUTS)
+def test_p2r_paper_scale_960k(dev, w_p2r, layout):
+    b = run(w_p2r, dev, layout)
+    rep = check(w_p2r, b, sample_indices(w_p2r.n))
+    assert rep["flagged"] == 0
+
+
+@pytest.mark.parametrize("precision", [kf.KF_FP32, kf.KF_FP64_UPDATE, kf.KF_JOSEPH])
+def test_precision_study_pt_0p2_to_100(dev, w_prec, precision):
+    for w in w_prec:
+        b = run(w, dev, (kf.KF_AOSOA, 32), precision)
+        check(w, b, sample_indices(w.n), VARIANT_FORM[precision])
+
+
+# ----------------------------------------------------------- edge cases
+
+@pytest.mark.parametrize("n", [1, 2, 31, 33, 127, 129, 1007])
+@pytest.mark.parametrize("layout", [(kf.KF_SOA, 0), (kf.KF_AOSOA, 128), (kf.KF_AOSOA, 16)])
+def test_ragged_sizes(dev, n, layout):
+    for w in (W.make_p2z(n, seed=n), W.make_p2r(1, n, seed=n)):
+        b = run(w, dev, layout)
+        check(w, b, np.arange(n))
+
+
+def test_empty_batch_launches_nothing(dev):
+    w = W.make_p2z(16, seed=2)
+    b = kf.upload(w, kf.KF_SOA, 0, dev)
+    b.state_out.fill_(123.0)
+    kf.kf_p2z_propagate_update(kf.make_params(w.bz), kf.make_layout(kf.KF_SOA, 0, 0), b.state_in,
+                               b.cov_in, b.state_out, b.cov_out, b.charge, b.hit, b.hit_cov,
+                               b.surf)
+    torch.cuda.synchronize()
+    assert torch.all(b.state_out == 123.0)
+
+
+@pytest.mark.parametrize("kind", [W.P2Z, W.P2R])
+def test_in_place_equals_out_of_place(dev, kind):
+    w = W.make_p2z(5000, seed=5) if kind == W.P2Z else W.make_p2r(1, 5000, seed=5)
+    b = run(w, dev, (kf.KF_AOSOA, 64))
+    ref = b.download()
+    b2 = kf.upload(w, kf.KF_AOSOA, 64, dev)
+    b2.run(in_place=True)
+    torch.cuda.synchronize()
+    b2.state_out, b2.cov_out = b2.state_in, b2.cov_in
+    got = b2.download()
+    for a, c in zip(ref, got):
+        assert np.array_equal(a, c)
+
+
+def test_per_track_surfaces(dev):
+    rng = np.random.default_rng(8)
+    w = W.make_p2z(3001, seed=8)
+    zs = rng.uniform(20.0, 120.0, w.n).astype(np.float32)
+    b = run(w, dev, (kf.KF_SOA, 0), surf=zs)
+    check(w, b, np.arange(w.n), surf=zs.astype(np.float64))
+    w = W.make_p2r(1, 3001, seed=9)
+    rs = rng.uniform(5.0, 60.0, w.n).astype(np.float32)
+    b = run(w, dev, (kf.KF_AOSOA, 32), surf=rs)
+    rep = check(w, b, np.arange(w.n), surf=rs.astype(np.float64))
+    assert rep["flagged"] > 0  # some low-pT tracks never reach the outer radii
+
+
+def test_degenerate_tracks(dev):
+    # unreachable cylinder, start outside, parallel to the plane, k = 0,
+    # a non-positive-definite hit covariance
+    w = W.make_p2r(1, 64, seed=10)
+    w.state[3, 0:8] = 1.0 / 0.2          # pT 0.2 GeV: rho 17.5 cm, just reaches r = 30
+    w.state[3, 8:16] = 1.0 / 0.1         # rho 8.8 cm: never reaches r = 30
+    w.state[0, 16:24] = 35.0             # starts outside
+    w.state[3, 24:32] = 0.0              # infinite momentum: straight line
+    w.hitcov[5, 32:40] = -1.0            # S not positive definite
+    b = run(w, dev)
+    rep = check(w, b, np.arange(w.n))
+    st = b.download()[2]
+    assert np.all(st[8:24] & kf.NO_INTERSECT) and np.all(st[32:40] & kf.S_NOT_PD)
+    assert rep["flagged"] >= 24
+    w = W.make_p2z(64, seed=11)
+    w.state[5, 0:8] = np.float32(np.pi / 2)  # parallel to the plane
+    w.state[3, 8:16] = 0.0
+    w.hitcov[0, 16:24] = -1.0
+    b = run(w, dev)
+    check(w, b, np.arange(w.n))
+    st = b.download()[2]
+    assert np.all(st[0:8] == kf.NO_INTERSECT) and np.all(st[16:24] & kf.S_NOT_PD)
+
+
+def test_offsets_beyond_2_to_31_elements(dev):
+    # 105M tracks: the covariance array holds > 2^31 floats, so element
+    # offsets need 64-bit arithmetic.  The batch repeats a 1M-track workload.
+    base = W.make_p2r(100, 10000, seed=12)
+    reps = 105
+    n = base.n * reps
+    lay = kf.make_layout(kf.KF_SOA, 0, n)
+
+    def rep_dev(a, dtype=torch.float32):
+        t = torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+        return t.repeat(1, reps).reshape(-1).contiguous() if t.dim() == 2 else t.repeat(reps)
+
+    st_in, cv_in = rep_dev(base.state), rep_dev(base.cov)
+    st_out, cv_out = torch.empty_like(st_in), torch.empty_like(cv_in)
+    status = torch.zeros(n, dtype=torch.uint8, device=dev)
+    kf.kf_p2r_propagate_update(kf.make_params(base.bz), lay, st_in, cv_in, st_out, cv_out,
+                               rep_dev(base.charge), rep_dev(base.hit), rep_dev(base.hitcov),
+                               torch.tensor([base.surf], device=dev), 0, status)
+    torch.cuda.synchronize()
+    idx = np.concatenate([np.arange(n - 3000, n), np.arange(0, n, n // 3000)])
+    gi = torch.from_numpy(idx).to(dev)
+    g_st = st_out.view(6, n)[:, gi].cpu().numpy().T
+    g_cv = cv_out.view(21, n)[:, gi].cpu().numpy().T
+    g_stat = status[gi].cpu().numpy()
+    bi = idx % base.n
+    o_st, o_cv, o_stat, _ = oracle_on(base, bi)
+    rep = compare.compare(g_st, g_cv, g_stat, o_st, o_cv, o_stat)
+    assert rep["ok"], rep
+    del st_in, cv_in, st_out, cv_out
+    torch.cuda.empty_cache()
+
+
+# --------------------------------------------------- argument refusal
+
+def test_bad_pointers_are_refused_not_launched(dev):
+    w = W.make_p2z(1000, seed=13)
+    b = kf.upload(w, kf.KF_SOA, 0, dev)
+    p = kf.make_params(w.bz)
+    lay = kf.make_layout(kf.KF_SOA, 0, w.n)
+    args = [b.state_in, b.cov_in, b.state_out, b.cov_out, b.charge, b.hit, b.hit_cov, b.surf]
+
+    def call(**over):
+        a = list(args)
+        for k, v in over.items():
+            a[int(k[1:])] = v
+        return kf.load().kf_p2z_propagate_update(
+            ctypes.byref(p), lay, *[t if isinstance(t, int) else t.data_ptr() for t in a], 0, None,
+            torch.cuda.current_stream().cuda_stream)
+
+    host = np.zeros(21 * w.n, dtype=np.float32)
+    assert call(a1=host.ctypes.data) == kf.KF_ERR_ARG          # pageable host memory
+    assert call(a2=b.state_out.data_ptr() + 4) == kf.KF_ERR_ARG  # misaligned
+    assert call(a2=b.state_in.data_ptr() + 16) == kf.KF_ERR_ARG  # partial overlap with state_in
+    torch.cuda.synchronize()
+    assert kf.kf_last_error_string() != ""
+
+
+def test_short_buffer_is_refused(dev):
+    # A buffer from its own cudaMalloc, smaller than the layout needs.
+    w = W.make_p2z(4096, seed=14)
+    b = kf.upload(w, kf.KF_SOA, 0, dev)
+    n_big = 1 << 22  # 4M tracks need 100 MB of covariance: more than any segment holds here
+    p = kf.make_params(w.bz)
+    rc = kf.load().kf_p2z_propagate_update(
+        ctypes.byref(p), kf.make_layout(kf.KF_SOA, 0, n_big), b.state_in.data_ptr(),
+        b.cov_in.data_ptr(), b.state_out.data_ptr(), b.cov_out.data_ptr(), b.charge.data_ptr(),
+        b.hit.data_ptr(), b.hit_cov.data_ptr(), b.surf.data_ptr(), 0, None,
+        torch.cuda.current_stream().cuda_stream)
+    assert rc == kf.KF_ERR_ARG
+    assert "allocation" in kf.kf_last_error_string()
+
+
+# ------------------------------------------------ host-array entry point
+
+@pytest.mark.parametrize("layout", [(kf.KF_SOA, 0), (kf.KF_AOSOA, 64)])
+@pytest.mark.parametrize("pinned", [True, False])
+def test_host_array_entry_matches_device_entry(dev, layout, pinned):
+    # 99,999 tracks in chunks of 16,384: seven chunks over both pipeline
+    # slots, the last one ragged.  Same kernel, so results are bitwise equal.
+    for w in (W.make_p2r(3, 33333, seed=15), W.make_p2z(99999, seed=16)):
+        hb = kf.host_upload(w, layout[0], layout[1], dev, chunk_tracks=16384, pinned=pinned)
+        hb.run()
+        torch.cuda.synchronize()
+        got = hb.download()
+        ref = run(w, dev, layout).download()
+        for a, c in zip(ref, got):
+            assert np.array_equal(a, c)
+        idx = sample_indices(w.n, 4000)
+        o_st, o_cv, o_stat, _ = oracle_on(w, idx)
+        rep = compare.compare(got[0].T[idx], got[1].T[idx], got[2][idx], o_st, o_cv, o_stat)
+        assert rep["ok"], rep
+
+
+def test_host_entry_rejects_small_workspace(dev):
+    w = W.make_p2z(5000, seed=17)
+    hb = kf.host_upload(w, kf.KF_SOA, 0, dev, chunk_tracks=1024)
+    hb.workspace = hb.workspace[: hb.workspace.numel() // 2]
+    with pytest.raises(kf.KfError) as e:
+        hb.run()
+    assert e.value.code == kf.KF_ERR_ARG

@@ -97,8 +97,7 @@ def test_p2r_matches_runge_kutta_lorentz_force():
     for p, q in sample_tracks(n=8, seed=5, pt=(0.6, 30.0)):
         R = 25.0
         po, _, st = oracle.propagate_to_r(p, q, BZ, R)
-        truth, s, reached = W.simulate_to_r(p.reshape(6, 1), np.array([q]), BZ, R, h=0.01,
-                                            bisect=60)
+        truth, s, reached = W.simulate_to_r(p.reshape(6, 1), np.array([q]), BZ, R, h=0.01)
         assert bool(reached[0]) == (st == 0)
         if st:
             continue
