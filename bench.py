@@ -54,6 +54,12 @@ def parse():
                     help="auto | soa | aosoa16 | aosoa32 | aosoa64 | aosoa128")
     ap.add_argument("--e2e-steps", type=int, default=30)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile-only", action="store_true",
+                    help="run a few launches of one layout and exit (for ncu captures)")
+    ap.add_argument("--kind", choices=["p2r", "p2z"], default="p2r",
+                    help="workload of --profile-only")
+    ap.add_argument("--e2e-chunk", type=int, default=0,
+                    help="tracks per pipeline chunk of the host-array call (0 = library default)")
     return ap.parse_args()
 
 
@@ -237,9 +243,21 @@ def main():
     if world > 1:
         dist.init_process_group("nccl", device_id=dev)
 
-    w = W.make_p2r(NEVTS, NTRKS, seed=1 + rank)
     layouts = {"soa": (kf.KF_SOA, 0), "aosoa16": (kf.KF_AOSOA, 16), "aosoa32": (kf.KF_AOSOA, 32),
                "aosoa64": (kf.KF_AOSOA, 64), "aosoa128": (kf.KF_AOSOA, 128)}
+
+    if args.profile_only:
+        w = (W.make_p2r(NEVTS, NTRKS, seed=1) if args.kind == "p2r"
+             else W.make_p2z(NEVTS * NTRKS, seed=1))
+        kind, width = layouts["aosoa16" if args.layout == "auto" else args.layout]
+        bs = [kf.upload(w, kind, width, dev) for _ in range(2)]
+        for i in range(5):
+            bs[i % 2].run()
+        torch.cuda.synchronize()
+        print(f"profile-only: {args.kind} n={w.n} layout={args.layout}: 5 launches done")
+        return 0
+
+    w = W.make_p2r(NEVTS, NTRKS, seed=1 + rank)
 
     def time_launches(batches, reps):
         torch.cuda.synchronize()
@@ -329,7 +347,7 @@ def main():
 
     # End to end through the host-array entry point (pinned host memory).
     e2e = None
-    hb = kf.host_upload(w, kind, width, dev, chunk_tracks=0, pinned=True)
+    hb = kf.host_upload(w, kind, width, dev, chunk_tracks=args.e2e_chunk, pinned=True)
     hb.run()
     torch.cuda.synchronize()
     ke = max(3, args.e2e_steps)

@@ -73,4 +73,12 @@ def compare(g_state, g_cov, g_status, o_state, o_cov, o_status,
     }
     rep["ok"] = bool(status_equal and rep["param"]["max"] <= tol_param
                      and rep["cov"]["max"] <= tol_cov)
+    if not rep["ok"] and len(o_status):
+        # the worst tracks, to make a failure readable
+        tp = int(np.argmax(pe.max(axis=1)))
+        tc = int(np.argmax(ce.max(axis=1)))
+        rep["worst_param"] = {"track": tp, "err": pe[tp].tolist(), "gpu": np.asarray(g_state)[tp].tolist(),
+                              "oracle": np.asarray(o_state)[tp].tolist()}
+        rep["worst_cov"] = {"track": tc, "err": ce[tc].tolist()}
+        rep["status_mismatch_tracks"] = np.nonzero(g_status != o_status)[0][:10].tolist()
     return rep

@@ -264,6 +264,8 @@ def upload(w: W.Workload, layout_kind: int = KF_SOA, width: int = 32, device="cu
     lay = make_layout(layout_kind, width, w.n)
     st_in = to_device(w.state, lay, device)
     cv_in = to_device(w.cov, lay, device)
+    if surf_per_track is None and np.ndim(w.surf) > 0:
+        surf_per_track = w.surf
     surf = (torch.tensor([w.surf], dtype=torch.float32, device=device) if surf_per_track is None
             else torch.from_numpy(np.ascontiguousarray(surf_per_track, dtype=np.float32)).to(device))
     return DeviceBatch(
@@ -335,8 +337,10 @@ def host_upload(w: W.Workload, layout_kind: int = KF_SOA, width: int = 32, devic
     cv_out = torch.empty_like(cv_in, pin_memory=pinned)
     q = torch.from_numpy(np.ascontiguousarray(w.charge))
     status = torch.zeros(w.n, dtype=torch.uint8)
-    surf = torch.tensor([w.surf], dtype=torch.float32)
+    surf = (torch.tensor([w.surf], dtype=torch.float32) if np.ndim(w.surf) == 0
+            else torch.from_numpy(np.ascontiguousarray(w.surf, dtype=np.float32)))
     if pinned:
+        surf = surf.pin_memory()
         q, status = q.pin_memory(), status.pin_memory()
     ws_bytes = kf_host_workspace_bytes(lay, chunk_tracks)
     ws = torch.empty(ws_bytes, dtype=torch.uint8, device=device)

@@ -49,7 +49,7 @@ class Workload:
     kind: int                      # P2Z or P2R
     n: int
     bz: float
-    surf: float                    # z of the plane (p2z) or r of the cylinder (p2r)
+    surf: object                   # z of the plane / r of the cylinder: float, or float32 [n]
     state: np.ndarray              # float32 [6, n] start state (smeared truth)
     cov: np.ndarray                # float32 [21, n]
     charge: np.ndarray             # int8 [n]
@@ -105,7 +105,7 @@ def simulate_to_z(truth: np.ndarray, q, bz: float, zt, steps: int = 64):
     return out, S
 
 
-def simulate_to_r(truth: np.ndarray, q, bz: float, R: float, h: float = 1.0,
+def simulate_to_r(truth: np.ndarray, q, bz: float, R, h: float = 1.0,
                   s_max: Optional[float] = None, refine: int = 8):
     """True state at the first outward crossing of radius R (float64 [6, n]).
 
@@ -116,8 +116,9 @@ def simulate_to_r(truth: np.ndarray, q, bz: float, R: float, h: float = 1.0,
     returned as NaN with reached = False."""
     x0, y0, z0, k, phi, th = [np.asarray(a, dtype=np.float64) for a in truth]
     n = x0.shape[0]
+    Rv = np.broadcast_to(np.asarray(R, dtype=np.float64), (n,))
     if s_max is None:
-        s_max = 4.0 * R
+        s_max = 4.0 * float(Rv.max()) if n else 0.0
     kappa = np.broadcast_to(curvature_rate(q, k, bz), (n,)).copy()
     X, Y = x0.copy(), y0.copy()
     TX, TY = np.cos(phi), np.sin(phi)
@@ -127,24 +128,25 @@ def simulate_to_r(truth: np.ndarray, q, bz: float, R: float, h: float = 1.0,
     out_tx = np.full(n, np.nan)
     out_ty = np.full(n, np.nan)
     out_s = np.full(n, np.nan)
-    R2 = R * R
-    active = np.nonzero(X * X + Y * Y < R2)[0]
+    R2all = Rv * Rv
+    active = np.nonzero(X * X + Y * Y < R2all)[0]
     nsteps = int(math.ceil(s_max / h))
     for _ in range(nsteps):
         if active.size == 0:
             break
         xa, ya, txa, tya, ka = X[active], Y[active], TX[active], TY[active], kappa[active]
+        R2 = R2all[active]
         xn, yn, txn, tyn = rk4_transverse(xa, ya, txa, tya, ka, h, 1)
         crossed = xn * xn + yn * yn >= R2
         if np.any(crossed):
             c = np.nonzero(crossed)[0]
-            xc, yc, txc, tyc, kc = xa[c], ya[c], txa[c], tya[c], ka[c]
+            xc, yc, txc, tyc, kc, R2c = xa[c], ya[c], txa[c], tya[c], ka[c], R2[c]
             # start from the straight-line estimate inside the step
             b = xc * txc + yc * tyc
-            f = np.clip(-b + np.sqrt(np.maximum(b * b - (xc * xc + yc * yc - R2), 0.0)), 0.0, h)
+            f = np.clip(-b + np.sqrt(np.maximum(b * b - (xc * xc + yc * yc - R2c), 0.0)), 0.0, h)
             for _it in range(refine):
                 xf, yf, txf, tyf = rk4_transverse(xc, yc, txc, tyc, kc, f, 1)
-                g = xf * xf + yf * yf - R2
+                g = xf * xf + yf * yf - R2c
                 dg = 2.0 * (xf * txf + yf * tyf)
                 f = np.clip(f - g / dg, 0.0, h)
             xf, yf, txf, tyf = rk4_transverse(xc, yc, txc, tyc, kc, f, 1)
@@ -224,6 +226,13 @@ def _smear(rng, truth, C):
     return start
 
 
+def _surface(v):
+    """A scalar surface position, or a float32 [n] array of them."""
+    if np.ndim(v) == 0:
+        return float(v)
+    return np.ascontiguousarray(v, dtype=np.float32)
+
+
 def make_p2z(n: int, seed: int = 1, pt_range=(0.5, 10.0), eta_range=(1.5, 2.5),
              zt: float = 50.0, bz: float = 3.8, hit_sigma: float = 0.01,
              rk4_steps: int = 24) -> Workload:
@@ -236,10 +245,10 @@ def make_p2z(n: int, seed: int = 1, pt_range=(0.5, 10.0), eta_range=(1.5, 2.5),
     surf_truth, _ = simulate_to_z(truth, q, bz, zt, steps=rk4_steps)
     hit = np.stack([surf_truth[0] + r_hit.normal(0, hit_sigma, n),
                     surf_truth[1] + r_hit.normal(0, hit_sigma, n),
-                    np.full(n, zt)])
+                    np.broadcast_to(np.asarray(zt, dtype=np.float64), (n,))])
     hitcov = np.zeros((6, n))
     hitcov[0] = hitcov[2] = hitcov[5] = hit_sigma ** 2
-    return Workload(kind=P2Z, n=n, bz=bz, surf=zt,
+    return Workload(kind=P2Z, n=n, bz=bz, surf=_surface(zt),
                     state=start.astype(np.float32), cov=pack_sym(C).astype(np.float32),
                     charge=q, hit=hit.astype(np.float32), hitcov=hitcov.astype(np.float32),
                     truth_start=truth, truth_surface=surf_truth,
@@ -260,16 +269,17 @@ def make_p2r(nevts: int, ntrks: int, seed: int = 1, pt_range=(0.5, 10.0),
     start = _smear(r_smear, truth, C)
     surf_truth, _, reached = simulate_to_r(truth, q, bz, R, h=rk4_h)
     phic = np.arctan2(surf_truth[1], surf_truth[0])
-    phih = np.where(reached, phic + r_hit.normal(0, rphi_sigma, n) / R, 0.0)
+    phih = np.where(reached, phic + r_hit.normal(0, rphi_sigma, n) / np.asarray(R), 0.0)
     zh = np.where(reached, surf_truth[2] + r_hit.normal(0, z_sigma, n), 0.0)
-    hit = np.stack([R * np.cos(phih), R * np.sin(phih), zh])
+    Rv = np.broadcast_to(np.asarray(R, dtype=np.float64), (n,))
+    hit = np.stack([Rv * np.cos(phih), Rv * np.sin(phih), zh])
     s, c = np.sin(phih), np.cos(phih)
     hitcov = np.zeros((6, n))
     hitcov[0] = rphi_sigma ** 2 * s * s      # xx
     hitcov[1] = -rphi_sigma ** 2 * s * c     # xy
     hitcov[2] = rphi_sigma ** 2 * c * c      # yy
     hitcov[5] = z_sigma ** 2                 # zz
-    return Workload(kind=P2R, n=n, bz=bz, surf=R,
+    return Workload(kind=P2R, n=n, bz=bz, surf=_surface(R),
                     state=start.astype(np.float32), cov=pack_sym(C).astype(np.float32),
                     charge=q, hit=hit.astype(np.float32), hitcov=hitcov.astype(np.float32),
                     truth_start=truth, truth_surface=surf_truth, reached=reached,
@@ -319,3 +329,126 @@ def precision_p2z(n: int = 1_000_000, seed: int = 3) -> Workload:
 def precision_p2r(n: int = 1_000_000, seed: int = 4) -> Workload:
     """Precision study, p2r half: pT extended to 0.2-100 GeV."""
     return make_p2r(100, n // 100, seed=seed, pt_range=(0.2, 100.0))
+
+
+# ------------------------------------------------------ multi-layer chain
+
+@dataclasses.dataclass
+class ChainWorkload:
+    n: int
+    bz: float
+    kinds: np.ndarray              # int32 [L]: P2Z or P2R per layer
+    pos: np.ndarray                # float32 [L]: z of the plane / r of the cylinder
+    event_sizes: np.ndarray        # int64 [E] tracks per event (tracks are event-major)
+    state: np.ndarray              # float32 [6, n]
+    cov: np.ndarray                # float32 [21, n]
+    charge: np.ndarray             # int8 [n]
+    hit: np.ndarray                # float32 [L, 3, n]
+    hitcov: np.ndarray             # float32 [L, 6, n]
+    truth_pool_layers: np.ndarray  # float64 [L, 6, m] pool's true states per surface (nan: not reached)
+    truth_index: np.ndarray        # int64 [n] pool entry of each track
+    description: str = ""
+
+    @property
+    def L(self) -> int:
+        return int(self.kinds.shape[0])
+
+    def truth_layer(self, l: int, idx=None) -> np.ndarray:
+        """True states [6, len(idx)] on surface l (NaN where not reached)."""
+        ti = self.truth_index if idx is None else self.truth_index[idx]
+        return self.truth_pool_layers[l][:, ti]
+
+
+def chain_layers(n_barrel: int = 8, n_endcap: int = 7, r_range=(4.0, 110.0),
+                 z_range=(30.0, 280.0)):
+    """Alternating barrel (p2r) and endcap (p2z) layers: r0, z0, r1, z1, ..."""
+    rs = np.linspace(r_range[0], r_range[1], n_barrel)
+    zs = np.linspace(z_range[0], z_range[1], n_endcap)
+    kinds, pos = [], []
+    for i in range(max(n_barrel, n_endcap)):
+        if i < n_barrel:
+            kinds.append(P2R)
+            pos.append(rs[i])
+        if i < n_endcap:
+            kinds.append(P2Z)
+            pos.append(zs[i])
+    return np.array(kinds, dtype=np.int32), np.array(pos, dtype=np.float32)
+
+
+def lognormal_event_sizes(rng, events: int, median: float = 5000.0, sigma: float = 1.0,
+                          lo: int = 500, hi: int = 40000) -> np.ndarray:
+    sizes = np.exp(rng.normal(math.log(median), sigma, events))
+    return np.clip(np.rint(sizes), lo, hi).astype(np.int64)
+
+
+def make_chain(events: int = 256, seed: int = 1, sizes: Optional[np.ndarray] = None,
+               pt_range=(0.5, 10.0), eta_range=(1.5, 2.5), bz: float = 3.8,
+               kinds: Optional[np.ndarray] = None, pos: Optional[np.ndarray] = None,
+               xy_sigma: float = 0.01, rphi_sigma: float = 0.01, z_sigma: float = 0.05,
+               pool: int = 65536, rk4_steps: int = 16, rk4_h: float = 1.0) -> ChainWorkload:
+    """Events of lognormal track counts run through a layer sequence.
+
+    As in the paper's mini-apps (section 2: a fixed set of track parameters,
+    smeared at random for every track), a pool of true tracks is simulated
+    through the layers once; every track takes a true track from the pool,
+    its own start-state smear N(0, C) and its own hit smear on each surface.
+    p2z planes may lie behind the track; a cylinder is taken at the first
+    outward crossing from inside.  Where the true track does not reach a
+    surface its hit is a placeholder and the truth is NaN."""
+    ss = np.random.SeedSequence(seed)
+    r_evt, r_trk, r_pick, r_cov, r_smear, r_hit = [np.random.Generator(np.random.PCG64(s))
+                                                   for s in ss.spawn(6)]
+    if kinds is None or pos is None:
+        kinds, pos = chain_layers()
+    if sizes is None:
+        sizes = lognormal_event_sizes(r_evt, events)
+    n = int(sizes.sum())
+    m = int(min(pool, n)) if pool else n
+    tpool, qpool = _draw_tracks(r_trk, m, pt_range, eta_range)
+    L = len(kinds)
+    # the pool's true states on every surface
+    ptl = np.full((L, 6, m), np.nan)
+    cur = tpool.copy()
+    alive = np.ones(m, dtype=bool)
+    for l in range(L):
+        if kinds[l] == P2Z:
+            nxt, _ = simulate_to_z(cur, qpool, bz, float(pos[l]), steps=rk4_steps)
+            ok = alive & np.isfinite(nxt[0])
+        else:
+            nxt, _, reached = simulate_to_r(cur, qpool, bz, float(pos[l]), h=rk4_h)
+            ok = alive & reached
+        ptl[l] = np.where(ok, nxt, np.nan)
+        cur = np.where(ok, nxt, cur)
+    idx = np.arange(n) % m if n == m else r_pick.integers(0, m, n)
+    truth = tpool[:, idx]
+    q = qpool[idx]
+    C = make_covariances(r_cov, truth[3])
+    start = _smear(r_smear, truth, C)
+    hit = np.zeros((L, 3, n), dtype=np.float32)
+    hitcov = np.zeros((L, 6, n), dtype=np.float32)
+    for l in range(L):
+        tx, ty, tz = ptl[l, 0][idx], ptl[l, 1][idx], ptl[l, 2][idx]
+        ok = np.isfinite(tx)
+        if kinds[l] == P2Z:
+            hit[l, 0] = np.where(ok, tx + r_hit.normal(0, xy_sigma, n), 0.0)
+            hit[l, 1] = np.where(ok, ty + r_hit.normal(0, xy_sigma, n), 0.0)
+            hit[l, 2] = pos[l]
+            hitcov[l, 0] = hitcov[l, 2] = hitcov[l, 5] = xy_sigma ** 2
+        else:
+            R = float(pos[l])
+            phic = np.arctan2(ty, tx)
+            phih = np.where(ok, phic + r_hit.normal(0, rphi_sigma, n) / R, 0.0)
+            hit[l, 0], hit[l, 1] = R * np.cos(phih), R * np.sin(phih)
+            hit[l, 2] = np.where(ok, tz + r_hit.normal(0, z_sigma, n), 0.0)
+            s, c = np.sin(phih), np.cos(phih)
+            hitcov[l, 0] = rphi_sigma ** 2 * s * s
+            hitcov[l, 1] = -rphi_sigma ** 2 * s * c
+            hitcov[l, 2] = rphi_sigma ** 2 * c * c
+            hitcov[l, 5] = z_sigma ** 2
+    return ChainWorkload(n=n, bz=bz, kinds=np.asarray(kinds, dtype=np.int32),
+                         pos=np.asarray(pos, dtype=np.float32), event_sizes=sizes,
+                         state=start.astype(np.float32), cov=pack_sym(C).astype(np.float32),
+                         charge=q, hit=hit, hitcov=hitcov, truth_pool_layers=ptl,
+                         truth_index=idx,
+                         description=(f"chain {len(sizes)} events, {n} tracks, {L} layers, "
+                                      f"{m} simulated true tracks"))

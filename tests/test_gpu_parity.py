@@ -59,7 +59,9 @@ def sample_indices(n, k=20000):
 
 
 def oracle_on(w, idx, form=oracle.FORM_STANDARD, surf=None):
-    s = w.surf if surf is None else surf[idx]
+    if surf is None:
+        surf = w.surf
+    s = surf[idx] if np.ndim(surf) > 0 else surf
     return oracle.step_batch(w.kind, w.state.T[idx], w.cov.T[idx], w.charge[idx], w.hit.T[idx],
                              w.hitcov.T[idx], s, w.bz, form, threads=8)
 
@@ -137,16 +139,17 @@ def test_in_place_equals_out_of_place(dev, kind):
 
 
 def test_per_track_surfaces(dev):
+    # every track has its own plane / cylinder and its hit lies on it
     rng = np.random.default_rng(8)
-    w = W.make_p2z(3001, seed=8)
-    zs = rng.uniform(20.0, 120.0, w.n).astype(np.float32)
-    b = run(w, dev, (kf.KF_SOA, 0), surf=zs)
-    check(w, b, np.arange(w.n), surf=zs.astype(np.float64))
-    w = W.make_p2r(1, 3001, seed=9)
-    rs = rng.uniform(5.0, 60.0, w.n).astype(np.float32)
-    b = run(w, dev, (kf.KF_AOSOA, 32), surf=rs)
-    rep = check(w, b, np.arange(w.n), surf=rs.astype(np.float64))
-    assert rep["flagged"] > 0  # some low-pT tracks never reach the outer radii
+    zs = rng.uniform(20.0, 120.0, 3001)
+    w = W.make_p2z(3001, seed=8, zt=zs)
+    b = run(w, dev, (kf.KF_SOA, 0))
+    check(w, b, np.arange(w.n))
+    rs = rng.uniform(5.0, 150.0, 3001)  # 2 rho = 88..175 cm for pT 0.5..1 GeV: some never get there
+    w = W.make_p2r(1, 3001, seed=9, R=rs)
+    b = run(w, dev, (kf.KF_AOSOA, 32))
+    rep = check(w, b, np.arange(w.n))
+    assert rep["flagged"] > 0 and rep["flagged"] == int(np.sum(~w.reached))
 
 
 def test_degenerate_tracks(dev):
