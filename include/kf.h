@@ -183,6 +183,59 @@ int kf_p2r_propagate_update_host(const kf_params *params, kf_layout layout,
  * `chunk_tracks` (0 = default chunk); -1 for an invalid layout. */
 int64_t kf_host_workspace_bytes(kf_layout layout, int64_t chunk_tracks);
 
+/* Step kinds for entry points that take the kind as an argument. */
+#define KF_P2Z 0
+#define KF_P2R 1
+
+/* Capacity of the staging buffer of kf_propagate_update_host_noalloc. */
+#define KF_NOALLOC_MAX_CHUNK     32768    /* tracks per staged chunk        */
+#define KF_NOALLOC_STAGING_BYTES 8454144  /* device bytes held per GPU      */
+
+/*
+ * kf_propagate_update_host_noalloc -- the host-array step (as
+ * kf_p2z_propagate_update_host / kf_p2r_propagate_update_host) for callers
+ * that cannot allocate device memory.  The paper has no counterpart; this
+ * entry point exists for deployment.
+ *
+ * Some callers cannot call cudaMalloc: a plugin or module whose process owns
+ * the device allocator and forbids others from allocating, or a latency-
+ * critical loop where cudaMalloc/cudaFree would synchronise the device.
+ * Such callers pass only host arrays.  This call stages them through a
+ * buffer of KF_NOALLOC_STAGING_BYTES (about 8 MiB) that the library itself
+ * declares in device memory: every GPU that loads the library holds that
+ * buffer until the process exits.  The call allocates nothing -- no
+ * cudaMalloc, no cudaFree, no stream or event creation.
+ *
+ *   kind            KF_P2Z or KF_P2R
+ *   params, layout, state_in ... status
+ *                   as for the _host calls: HOST pointers, the same layouts
+ *                   and sizes; status may be NULL; surf is a host scalar or a
+ *                   host [n] array.
+ *   chunk_tracks    tracks per staged chunk, 0 = KF_NOALLOC_MAX_CHUNK; a
+ *                   value above KF_NOALLOC_MAX_CHUNK is rejected with
+ *                   KF_ERR_ARG.  Any n is accepted: the batch is processed
+ *                   chunk by chunk.
+ *   stream          all copies and kernels run on this stream, in order;
+ *                   synchronise it before reading the host outputs.
+ *
+ * Set-up: the first call on a device looks up the device address of the
+ * staging buffer with that device current (cudaGetSymbolAddress).  Make that
+ * first call before any stream capture.
+ * Sharing: every call on a device uses the same staging buffer, which keeps
+ * the last call's contents (nothing in it needs to start at zero).  Calls
+ * whose work overlaps on the GPU -- on different streams, or from different
+ * host threads without ordering between them -- race on the buffer and
+ * corrupt each other's results: keep them on one stream or order them.
+ */
+int kf_propagate_update_host_noalloc(int32_t kind, const kf_params *params,
+                                     kf_layout layout, const float *state_in,
+                                     const float *cov_in, float *state_out,
+                                     float *cov_out, const int8_t *charge,
+                                     const float *hit, const float *hit_cov,
+                                     const float *surf, int32_t surf_per_track,
+                                     uint8_t *status, int64_t chunk_tracks,
+                                     void *stream);
+
 /* Library version as MAJOR*10000 + MINOR*100 + PATCH. */
 int kf_version(void);
 

@@ -65,6 +65,9 @@ def load():
         fn = getattr(lib, name)
         fn.argtypes = host_args
         fn.restype = ctypes.c_int
+    lib.kf_propagate_update_host_noalloc.argtypes = [ctypes.c_int32] + step_args[:-1] + [
+        ctypes.c_int64, _VP]
+    lib.kf_propagate_update_host_noalloc.restype = ctypes.c_int
     lib.kf_host_workspace_bytes.argtypes = [kf_layout, ctypes.c_int64]
     lib.kf_host_workspace_bytes.restype = ctypes.c_int64
     lib.kf_version.restype = ctypes.c_int
@@ -190,6 +193,27 @@ def kf_p2r_propagate_update_host(params, layout, state_in, cov_in, state_out, co
     _step_host("kf_p2r_propagate_update_host", params, layout, state_in, cov_in, state_out,
                cov_out, charge, hit, hit_cov, r_surf, surf_per_track, status, workspace,
                chunk_tracks, stream)
+
+
+KF_P2Z, KF_P2R = 0, 1
+KF_NOALLOC_MAX_CHUNK = 32768
+
+
+def kf_propagate_update_host_noalloc(kind, params, layout, state_in, cov_in, state_out, cov_out,
+                                     charge, hit, hit_cov, surf, surf_per_track=0, status=None,
+                                     chunk_tracks=0, stream=None):
+    """C-ABI kf_propagate_update_host_noalloc: host arrays in and out, staged
+    through the library's fixed device buffer (no device allocation)."""
+    lib = load()
+    f32, i8, u8 = torch.float32, torch.int8, torch.uint8
+    rc = lib.kf_propagate_update_host_noalloc(
+        int(kind), ctypes.byref(params), layout,
+        _host_ptr(state_in, "state_in", f32), _host_ptr(cov_in, "cov_in", f32),
+        _host_ptr(state_out, "state_out", f32), _host_ptr(cov_out, "cov_out", f32),
+        _host_ptr(charge, "charge", i8), _host_ptr(hit, "hit", f32),
+        _host_ptr(hit_cov, "hit_cov", f32), _host_ptr(surf, "surf", f32), int(surf_per_track),
+        _host_ptr(status, "status", u8), int(chunk_tracks), _stream(stream))
+    _check(rc)
 
 
 def kf_host_workspace_bytes(layout, chunk_tracks: int = 0) -> int:
