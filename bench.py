@@ -41,7 +41,8 @@ NEVTS, NTRKS, RADIUS = 100, 9600, 30.0
 BYTES_PER_TRACK_P2R = 253
 FALLBACK_HBM_GBS = 6800.0
 KERNEL_SOURCES = ("paper_2401_14221_gb300/csrc/kf_device.cuh",
-                  "paper_2401_14221_gb300/csrc/kf_step.cu")
+                  "paper_2401_14221_gb300/csrc/kf_step.cu",
+                  "paper_2401_14221_gb300/csrc/kf_step_staged.cu")
 
 
 def parse():
@@ -52,8 +53,12 @@ def parse():
     ap.add_argument("--impl", choices=["kf", "reference"], default="kf")
     ap.add_argument("--layout", default="auto",
                     help="auto | soa | aosoa16 | aosoa32 | aosoa64 | aosoa128")
+    ap.add_argument("--step-kernel", default="auto", choices=["auto", "direct", "staged"])
     ap.add_argument("--e2e-steps", type=int, default=30)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-chain", action="store_true",
+                    help="skip the fused-chain vs per-layer-launch comparison")
+    ap.add_argument("--chain-steps", type=int, default=10)
     ap.add_argument("--profile-only", action="store_true",
                     help="run a few launches of one layout and exit (for ncu captures)")
     ap.add_argument("--kind", choices=["p2r", "p2z"], default="p2r",
@@ -220,6 +225,69 @@ def cpu_baseline(w):
                       f"{time.process_time() - c0:.1f} s CPU time"}
 
 
+def chain_bench(args, kf, W, dev, rank):
+    """Fused 15-layer chain vs the same chain as 15 single-step launches, on
+    the 256-event workload (lognormal event sizes).  Both run in place, so the
+    start state is restored before every timed run, outside the timed pair."""
+    import torch
+
+    from paper_2401_14221_gb300 import shard
+
+    cw = W.make_chain(events=256, seed=shard.rank_seed(7, rank))
+    dc = kf.chain_upload(cw, kf.KF_AOSOA, 32, dev)
+    L = cw.L
+    # per-layer launches captured once in a CUDA graph
+    stream = torch.cuda.Stream()
+    plain_graph = None
+    try:
+        dc.reset()
+        with torch.cuda.stream(stream):
+            dc.run_plain(stream=stream)
+        torch.cuda.synchronize()
+        plain_graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(plain_graph, stream=stream):
+            dc.run_plain()
+        torch.cuda.synchronize()
+    except Exception:
+        plain_graph = None
+
+    def timed(fn, reps):
+        ms = []
+        for _ in range(reps):
+            dc.reset()
+            torch.cuda.synchronize()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            fn()
+            b.record()
+            torch.cuda.synchronize()
+            ms.append(a.elapsed_time(b))
+        return sorted(ms)[len(ms) // 2]
+
+    reps = max(3, args.chain_steps)
+    timed(dc.run, 2)
+    fused_ms = timed(dc.run, reps)
+    plain_fn = plain_graph.replay if plain_graph is not None else dc.run_plain
+    timed(plain_fn, 2)
+    plain_ms = timed(plain_fn, reps)
+    # algorithmic bytes per track: fused reads state, cov, charge once (109 B),
+    # hits + hit covariances per layer (36 B each), writes state + cov (108 B);
+    # plain launches move 253 B per track per layer
+    fused_b = 109 + 36 * L + 108
+    plain_b = 253 * L
+    return {"workload": f"{len(cw.event_sizes)} events, {cw.n} tracks (lognormal sizes, median "
+                        f"5000, clipped 500-40000), {L} alternating layers",
+            "tracks": cw.n, "layers": L,
+            "fused_ms": fused_ms, "fused_tracks_per_s": cw.n / (fused_ms * 1e-3),
+            "plain_ms": plain_ms, "plain_tracks_per_s": cw.n / (plain_ms * 1e-3),
+            "speedup": plain_ms / fused_ms,
+            "fused_GBps": fused_b * cw.n / (fused_ms * 1e-3) / 1e9,
+            "plain_GBps": plain_b * cw.n / (plain_ms * 1e-3) / 1e9,
+            "bytes_per_track": {"fused": fused_b, "plain": plain_b},
+            "plain_launch": "CUDA graph" if plain_graph is not None else "eager",
+            "timing": f"median of {reps} runs, CUDA events, state reset outside the timed pair"}
+
+
 def main():
     args = parse()
     rank = int(os.environ.get("RANK", "0"))
@@ -234,6 +302,7 @@ def main():
 
     from paper_2401_14221_gb300 import build as kbuild
     from paper_2401_14221_gb300 import kf
+    from paper_2401_14221_gb300 import shard
     from paper_2401_14221_gb300 import workload as W
 
     if not kbuild.up_to_date():
@@ -250,6 +319,8 @@ def main():
         w = (W.make_p2r(NEVTS, NTRKS, seed=1) if args.kind == "p2r"
              else W.make_p2z(NEVTS * NTRKS, seed=1))
         kind, width = layouts["aosoa16" if args.layout == "auto" else args.layout]
+        kf.kf_set_step_kernel({"auto": kf.KF_STEP_AUTO, "direct": kf.KF_STEP_DIRECT,
+                               "staged": kf.KF_STEP_STAGED}[args.step_kernel])
         bs = [kf.upload(w, kind, width, dev) for _ in range(2)]
         for i in range(5):
             bs[i % 2].run()
@@ -257,7 +328,7 @@ def main():
         print(f"profile-only: {args.kind} n={w.n} layout={args.layout}: 5 launches done")
         return 0
 
-    w = W.make_p2r(NEVTS, NTRKS, seed=1 + rank)
+    w = W.make_p2r(NEVTS, NTRKS, seed=shard.rank_seed(1, rank))
 
     def time_launches(batches, reps):
         torch.cuda.synchronize()
@@ -269,18 +340,30 @@ def main():
         torch.cuda.synchronize()
         return a.elapsed_time(b) / reps
 
-    # Layout sweep (outside the timed region): SoA vs AoSoA block widths.
+    # Kernel x layout sweep (outside the timed region): the direct kernel on
+    # SoA and AoSoA, the staged kernel on AoSoA block widths.
+    modes = {"direct": kf.KF_STEP_DIRECT, "staged": kf.KF_STEP_STAGED}
     sweep = {}
-    if args.layout == "auto":
-        for name, (kind, width) in layouts.items():
+    if args.layout == "auto" or args.step_kernel == "auto":
+        for lname, (kind, width) in layouts.items():
+            if args.layout != "auto" and lname != args.layout:
+                continue
             bs = [kf.upload(w, kind, width, dev) for _ in range(2)]
-            time_launches(bs, 20)
-            ms = time_launches(bs, 200)
-            sweep[name] = {"ms": ms, "tracks_per_s": w.n / (ms * 1e-3)}
+            for mname, mode in modes.items():
+                if kind == kf.KF_SOA and mname == "staged":
+                    continue
+                if args.step_kernel != "auto" and mname != args.step_kernel:
+                    continue
+                kf.kf_set_step_kernel(mode)
+                time_launches(bs, 20)
+                ms = time_launches(bs, 200)
+                sweep[f"{mname}/{lname}"] = {"ms": ms, "tracks_per_s": w.n / (ms * 1e-3)}
             del bs
-        chosen = min(sweep, key=lambda k: sweep[k]["ms"])
+        best = min(sweep, key=lambda k: sweep[k]["ms"])
+        chosen_kernel, chosen = best.split("/")
     else:
-        chosen = args.layout
+        chosen_kernel, chosen = args.step_kernel, args.layout
+    kf.kf_set_step_kernel(modes[chosen_kernel])
     kind, width = layouts[chosen]
     sets = [kf.upload(w, kind, width, dev) for _ in range(4)]
 
@@ -321,24 +404,18 @@ def main():
     sampler = ClockSampler(gpu_id)
     sampler.start()
     time.sleep(0.3)
-    if world > 1:
-        dist.barrier()
+    shard.barrier(world)
     torch.cuda.synchronize()
     t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     t0.record()
     run_steps(args.steps)
     t1.record()
     torch.cuda.synchronize()
-    if world > 1:
-        dist.barrier()
+    shard.barrier(world)
     clocks = sampler.stop()
-    elapsed_ms = t0.elapsed_time(t1)
-    if world > 1:
-        t = torch.tensor([elapsed_ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        elapsed_ms = float(t.item())
+    elapsed_ms = shard.max_over_ranks(t0.elapsed_time(t1), world, dev)
     ms_per_step = elapsed_ms / args.steps
-    value = world * w.n * args.steps / (elapsed_ms * 1e-3)
+    value = shard.whole_job_throughput(w.n, args.steps, world, elapsed_ms * 1e-3)
 
     # Roofline of the step kernel: algorithmic bytes / average launch time.
     peak, peak_src = measured_hbm_peak()
@@ -352,22 +429,21 @@ def main():
     torch.cuda.synchronize()
     ke = max(3, args.e2e_steps)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    if world > 1:
-        dist.barrier()
+    shard.barrier(world)
     e0.record()
     for _ in range(ke):
         hb.run()
     e1.record()
     torch.cuda.synchronize()
-    e2e_ms = e0.elapsed_time(e1) / ke
-    if world > 1:
-        t = torch.tensor([e2e_ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_ms = float(t.item())
-    e2e = {"value": world * w.n / (e2e_ms * 1e-3), "unit": UNIT,
+    e2e_ms = shard.max_over_ranks(e0.elapsed_time(e1) / ke, world, dev)
+    e2e = {"value": shard.whole_job_throughput(w.n, 1, world, e2e_ms * 1e-3), "unit": UNIT,
            "h2d_bytes_per_step": hb.h2d_bytes(), "d2h_bytes_per_step": hb.d2h_bytes(),
            "ms_per_step": e2e_ms, "host_memory": "pinned"}
     del hb
+
+    chain = None
+    if not args.no_chain:
+        chain = chain_bench(args, kf, W, dev, rank)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -380,6 +456,7 @@ def main():
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic",
             "config": {"workload": workload_name(), "tracks": w.n, "layout": chosen,
+                       "step_kernel": chosen_kernel,
                        "precision": "fp32 standard-form update",
                        "l2": "inputs 139 MB + outputs 104 MB per step (> 126 MB L2), "
                              "rotated over 4 buffer sets",
@@ -388,11 +465,13 @@ def main():
                          "frac": achieved / peak, "traffic": traffic,
                          "peak_source": peak_src,
                          "bytes_per_track": BYTES_PER_TRACK_P2R},
+            "chain": chain,
             "cpu_baseline": cpu,
             "e2e": e2e,
             "gpu_launches": args.steps,
             "clocks": clocks,
-            "layout_sweep": sweep,
+            "sweep": sweep,
+            "device_error": kf.kf_take_device_error(),
         }
         print(json.dumps(line), flush=True)
     if world > 1:

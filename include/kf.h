@@ -187,6 +187,71 @@ int64_t kf_host_workspace_bytes(kf_layout layout, int64_t chunk_tracks);
 #define KF_P2Z 0
 #define KF_P2R 1
 
+/*
+ * kf_propagate_update_compressed -- the single step (kind KF_P2Z or KF_P2R)
+ * on a compressed covariance store: per track six FP32 standard deviations
+ * sigma_i = sqrt(C_ii) and fifteen FP16 correlations
+ * rho_ij = C_ij / (sigma_i sigma_j), stored as IEEE binary16 bit patterns, in
+ * packed off-diagonal order (10, 20, 21, 30, 31, 32, 40, ..., 54).
+ *   sigma_in/out   [6 comps] float in the layout
+ *   rho_in/out     [15 comps] uint16 in the layout (SoA [15][n]; AoSoA
+ *                  [ceil(n/W)][15][W])
+ *   other arguments as for kf_p2z_propagate_update / kf_p2r_propagate_update.
+ * The step decodes C_ii = sigma_i^2, C_ij = rho_ij sigma_i sigma_j, runs the
+ * FP32 step and encodes the result (sigma = sqrt(max(C_ii, 0)), rho clamped
+ * to [-1, 1], 0 where a sigma is 0, round to nearest).  FP16 keeps each
+ * correlation to 2^-12, i.e. each covariance element to about 2.4e-4 of
+ * sqrt(C_ii C_jj).  A track that is not propagated (KF_NO_INTERSECT) keeps
+ * its input sigma and rho bit for bit.  Traffic per p2r track: 193 B instead
+ * of 253 B.  No paper counterpart: a storage option of this library.
+ */
+int kf_propagate_update_compressed(int32_t kind, const kf_params *params,
+                                   kf_layout layout, const float *state_in,
+                                   const float *sigma_in,
+                                   const uint16_t *rho_in, float *state_out,
+                                   float *sigma_out, uint16_t *rho_out,
+                                   const int8_t *charge, const float *hit,
+                                   const float *hit_cov, const float *surf,
+                                   int32_t surf_per_track, uint8_t *status,
+                                   void *stream);
+
+/* ------------------------------------------------------------ the chain */
+#define KF_MAX_LAYERS 64
+
+typedef struct {
+    int32_t kind; /* KF_P2Z (plane at z = pos) or KF_P2R (cylinder r = pos) */
+    float   pos;  /* z of the plane or radius of the cylinder, cm          */
+} kf_layer;
+
+/*
+ * kf_kalman_chain -- the multi-layer track fit of the mini-apps (paper
+ * section 2 and the layer loop of Figs. 3-5: for every layer, propagateToZ or
+ * propagateToR, then KalmanUpdate), fused: each track runs through all L
+ * layers in one kernel with its state and covariance in registers.
+ *   params          field and update variant
+ *   layout          layout of the per-track arrays (as for the single step)
+ *   state, cov      [6 comps], [21 comps]: the start track on input, the
+ *                   track after the last layer on output (in place)
+ *   charge          [n] int8
+ *   hits            L consecutive hit arrays, layer l at
+ *                   hits + l * F3 floats, F3 = floats of a 3-component array
+ *                   in the layout (3n for SoA, 3 W ceil(n/W) for AoSoA)
+ *   hit_covs        L consecutive packed 3x3 hit-covariance arrays, layer l
+ *                   at hit_covs + l * F6 floats
+ *   layers          HOST array of L layer descriptors, 0 <= L <= KF_MAX_LAYERS
+ *   status          [n] uint8: OR of the per-layer status bits, or NULL
+ *   stream          cudaStream_t
+ * A layer the track does not reach is skipped (KF_NO_INTERSECT is set, the
+ * track is left as it was) and the chain goes on with the next layer; a
+ * layer whose update is rejected (KF_S_NOT_PD) leaves the propagated track.
+ * Same arithmetic as the single-step calls: chain over one layer equals the
+ * single step bit for bit.
+ */
+int kf_kalman_chain(const kf_params *params, kf_layout layout, float *state,
+                    float *cov, const int8_t *charge, const float *hits,
+                    const float *hit_covs, const kf_layer *layers, int32_t L,
+                    uint8_t *status, void *stream);
+
 /* Capacity of the staging buffer of kf_propagate_update_host_noalloc. */
 #define KF_NOALLOC_MAX_CHUNK     32768    /* tracks per staged chunk        */
 #define KF_NOALLOC_STAGING_BYTES 8454144  /* device bytes held per GPU      */
@@ -235,6 +300,111 @@ int kf_propagate_update_host_noalloc(int32_t kind, const kf_params *params,
                                      const float *surf, int32_t surf_per_track,
                                      uint8_t *status, int64_t chunk_tracks,
                                      void *stream);
+
+/* ----------------------------------------------------- the serving loop */
+/*
+ * A kf_server serves the multi-layer chain to a stream of events (requests)
+ * with continuous batching.  No paper counterpart: the paper's mini-apps run
+ * one fixed batch; this is the deployment form of the same chain.
+ *
+ * Events are submitted from any host thread at any time.  The server's
+ * scheduler thread admits pending events in submission order while an event
+ * slot (max_events_in_flight) and space in the caller's device arena are
+ * free, copies each one in, and whenever the device is not already computing
+ * a batch launches ONE kernel over every admitted event whose copies have
+ * landed (at most 128).  Events submitted while a batch runs join the next
+ * batch; results are copied out while the next batch computes.  Each track
+ * runs the same arithmetic as kf_kalman_chain (SoA layout, one event per
+ * submission), so an event's results do not depend on what else is in its
+ * batch.  Creating a server creates its thread, three streams and
+ * max_events_in_flight + 1 CUDA events; submitting and serving allocate
+ * nothing (event memory comes from the arena).
+ */
+typedef struct kf_server kf_server;
+
+typedef struct {
+    float    bz;                       /* field, T                              */
+    int32_t  precision;                /* KF_FP32 / KF_FP64_UPDATE / KF_JOSEPH  */
+    int32_t  L;                        /* layers of every event, 1..KF_MAX_LAYERS */
+    kf_layer layers[KF_MAX_LAYERS];
+    void    *arena;                    /* DEVICE memory owned by the caller,
+                                          256-byte aligned, untouched outside
+                                          the server until kf_server_destroy */
+    int64_t  arena_bytes;
+    int32_t  max_events_in_flight;     /* admitted and not yet finished, >= 1 */
+    int32_t  device;                   /* CUDA device of the arena             */
+} kf_server_config;
+
+typedef struct {
+    int64_t events_done;
+    int64_t tracks_done;
+    int64_t batches;                   /* kernel launches                      */
+    int64_t max_batch_events;          /* most events in one launch            */
+    double  p50_ms, p99_ms, max_ms, mean_ms; /* submit -> results in host memory */
+} kf_server_stats;
+
+/* Arena bytes one event of n tracks and L layers occupies (-1 if invalid). */
+int64_t kf_server_event_bytes(int64_t n, int32_t L);
+
+/* Create a server (starts its thread).  KF_ERR_ARG for a bad config or an
+ * arena that is not device memory of the stated size. */
+int kf_server_create(const kf_server_config *cfg, kf_server **out);
+
+/*
+ * Submit one event of n tracks.  HOST arrays, SoA per event: state [6][n],
+ * cov [21][n] packed, charge [n], hits [L][3][n], hit_covs [L][6][n]; results
+ * are written to state_out [6][n], cov_out [21][n] and status_out [n]
+ * (status_out may be NULL).  The arrays must stay valid until the event is
+ * done; page-locked memory lets the copies overlap.  Returns at once with a
+ * ticket.  KF_ERR_ARG if the event can never fit the arena.
+ */
+int kf_server_submit(kf_server *s, int64_t n, const float *state,
+                     const float *cov, const int8_t *charge, const float *hits,
+                     const float *hit_covs, float *state_out, float *cov_out,
+                     uint8_t *status_out, uint64_t *ticket);
+
+/* *done = 1 once the event's results are in host memory. */
+int kf_server_poll(kf_server *s, uint64_t ticket, int32_t *done);
+
+/* Block until the event is done (KF_OK; the ticket is then released) or
+ * timeout_s seconds pass (KF_ERR_TIMEOUT; the ticket stays valid). */
+int kf_server_wait(kf_server *s, uint64_t ticket, double timeout_s);
+
+/* paused != 0: admit and launch nothing new (work already on the device
+ * finishes); 0: resume. */
+int kf_server_pause(kf_server *s, int32_t paused);
+
+int kf_server_get_stats(kf_server *s, kf_server_stats *out);
+int kf_server_reset_stats(kf_server *s);
+
+/* Finish admitted and pending work (up to 30 s), stop the thread, release
+ * the server's streams and events.  The arena is the caller's again. */
+int kf_server_destroy(kf_server *s);
+
+/*
+ * kf_set_step_kernel -- choose the single-step kernel for all later calls in
+ * this process (a tuning knob; the results are the same, bit for bit):
+ *   KF_STEP_AUTO    (default) the staged kernel for AoSoA layouts, the direct
+ *                   kernel for SoA;
+ *   KF_STEP_DIRECT  one thread per track with direct global loads (any layout);
+ *   KF_STEP_STAGED  a persistent kernel in which a producer warp streams AoSoA
+ *                   tiles into shared memory with bulk asynchronous copies
+ *                   while eight warps compute (SoA falls back to direct).
+ * Returns KF_ERR_ARG for an unknown mode.
+ */
+#define KF_STEP_AUTO   0
+#define KF_STEP_DIRECT 1
+#define KF_STEP_STAGED 2
+int kf_set_step_kernel(int32_t mode);
+
+/*
+ * kf_take_device_error -- read and clear the library's device error word
+ * (synchronous).  Kernels that wait on barriers bound every wait; a wait
+ * that gives up sets KF_DEVERR_TIMEOUT here and the kernel ends early, so
+ * its results are incomplete.  *error_bits = 0 means no kernel gave up.
+ */
+#define KF_DEVERR_TIMEOUT 1u
+int kf_take_device_error(unsigned int *error_bits);
 
 /* Library version as MAJOR*10000 + MINOR*100 + PATCH. */
 int kf_version(void);

@@ -8,6 +8,16 @@ scale of the pair, so that near-zero off-diagonal entries are not judged
 relative to themselves; where o_ii o_jj = 0 (the z row after a p2z step)
 the entry must be exactly zero.  Bounds: 1e-4 on parameters, 1e-3 on
 covariance elements.
+
+A track on a cylinder has no variance along the surface normal, so its
+Cartesian (x, y) block is singular along a direction set by the crossing
+angle; an element such as C_xx = sin^2(a) C_tt is then as sensitive to a as
+1/a.  For such tracks the covariances are compared in the surface frame
+(t, r, z, k, phi, theta) of the oracle's crossing point, where the radial
+row is compared against the tangential scale.  Optionally an absolute floor
+eps_floor * sqrt(P_ii P_jj) is added, P being the oracle's covariance before
+the update: the update subtracts quantities of that scale, so no FP32
+computation can be closer than a few units of 2^-24 times it.
 """
 from __future__ import annotations
 
@@ -43,6 +53,51 @@ def cov_errors(g: np.ndarray, o: np.ndarray) -> np.ndarray:
     return err
 
 
+def unpack(c21: np.ndarray) -> np.ndarray:
+    """[n, 21] -> [n, 6, 6]."""
+    c21 = np.asarray(c21, dtype=np.float64)
+    out = np.empty((c21.shape[0], 6, 6))
+    k = 0
+    for i in range(6):
+        for j in range(i + 1):
+            out[:, i, j] = out[:, j, i] = c21[:, k]
+            k += 1
+    return out
+
+
+def pack(C: np.ndarray) -> np.ndarray:
+    return np.stack([C[:, i, j] for i, j in _TRI], axis=1)
+
+
+def surface_frame(cov: np.ndarray, angle: np.ndarray) -> np.ndarray:
+    """Rotate packed covariances [n, 21] so that components 0, 1 become the
+    tangential and radial position coordinates at azimuth `angle`."""
+    C = unpack(cov)
+    Q = np.tile(np.eye(6), (C.shape[0], 1, 1))
+    s, c = np.sin(angle), np.cos(angle)
+    Q[:, 0, 0], Q[:, 0, 1], Q[:, 1, 0], Q[:, 1, 1] = -s, c, c, s
+    return pack(np.einsum("nij,njk,nlk->nil", Q, C, Q))
+
+
+def cov_errors_frame(g: np.ndarray, o: np.ndarray, angle: np.ndarray,
+                     prior: np.ndarray = None, eps_floor: float = 0.0) -> np.ndarray:
+    """Covariance errors in the surface frame at `angle` (radial row judged on
+    the tangential scale), with an optional absolute floor from `prior`."""
+    gf, of = surface_frame(g, angle), surface_frame(o, angle)
+    diag = of[:, _DIAG].copy()
+    diag[:, 1] = diag[:, 0]  # the radial variance is structurally zero
+    scale = np.stack([np.sqrt(np.abs(diag[:, i] * diag[:, j])) for i, j in _TRI], axis=1)
+    if prior is not None and eps_floor > 0.0:
+        pf = surface_frame(prior, angle)
+        pd = pf[:, _DIAG].copy()
+        pd[:, 1] = pd[:, 0]
+        pscale = np.stack([np.sqrt(np.abs(pd[:, i] * pd[:, j])) for i, j in _TRI], axis=1)
+        scale = scale + eps_floor / TOL_COV * pscale
+    d = np.abs(gf - of)
+    with np.errstate(divide="ignore", invalid="ignore"):
+        return np.where(scale > 0, d / np.where(scale > 0, scale, 1.0), np.where(d == 0, 0.0, np.inf))
+
+
 def summary(err: np.ndarray) -> dict:
     if err.size == 0:
         return {"max": 0.0, "p99": 0.0, "mean": 0.0}
@@ -52,13 +107,22 @@ def summary(err: np.ndarray) -> dict:
 
 
 def compare(g_state, g_cov, g_status, o_state, o_cov, o_status,
-            tol_param: float = TOL_PARAM, tol_cov: float = TOL_COV) -> dict:
+            tol_param: float = TOL_PARAM, tol_cov: float = TOL_COV,
+            on_cylinder=None, prior=None, eps_floor: float = 0.0) -> dict:
     """All arrays per track ([n, 6], [n, 21], [n]).  Returns a report dict with
-    'ok', error summaries per component and the status agreement."""
+    'ok', error summaries per component and the status agreement.
+    on_cylinder: bool [n], tracks whose covariances are compared in the
+    surface frame of the oracle's point; prior/eps_floor: see module doc."""
     g_status = np.asarray(g_status).astype(np.int64)
     o_status = np.asarray(o_status).astype(np.int64)
     pe = param_errors(g_state, o_state)
     ce = cov_errors(g_cov, o_cov)
+    if on_cylinder is not None and np.any(on_cylinder):
+        m = np.asarray(on_cylinder, dtype=bool)
+        os_ = np.asarray(o_state, dtype=np.float64)
+        ang = np.arctan2(os_[m, 1], os_[m, 0])
+        pr = None if prior is None else np.asarray(prior)[m]
+        ce[m] = cov_errors_frame(np.asarray(g_cov)[m], np.asarray(o_cov)[m], ang, pr, eps_floor)
     status_equal = bool(np.array_equal(g_status, o_status))
     rep = {
         "n": int(len(o_status)),

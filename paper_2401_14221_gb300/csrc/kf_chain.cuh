@@ -1,0 +1,66 @@
+// kf_chain.cuh -- per-track body of the multi-layer chain (paper section 2
+// and the layer loop of Figs. 3-5: propagateTo{Z,R} then KalmanUpdate for
+// every layer), shared by the single-launch chain kernel and the serving
+// loop's batched kernel.
+#pragma once
+
+#include <cstdint>
+
+#include "kf_device.cuh"
+
+namespace kf {
+
+struct ChainLoc {
+  int64_t base;
+  int64_t stride;
+};
+
+// Element (c, i) of a C-component array sits at base + c * stride.
+template <int C>
+__device__ __forceinline__ ChainLoc chain_locate(int64_t i, int64_t n, int32_t soa, int32_t lw) {
+  if (soa) return {i, n};
+  const int64_t W = int64_t(1) << lw;
+  return {(i >> lw) * (C * W) + (i & (W - 1)), W};
+}
+
+struct LayerHit {
+  float hx, hy, hz, hc[6];
+};
+
+__device__ __forceinline__ void load_layer_hit(const float *hits, int64_t hit_stride,
+                                               const float *hitcovs, int64_t hc_stride, int l,
+                                               const ChainLoc &l3, const ChainLoc &l6,
+                                               LayerHit &h) {
+  const float *hp = hits + l * hit_stride + l3.base;
+  const float *cp = hitcovs + l * hc_stride + l6.base;
+  h.hx = __ldg(hp);
+  h.hy = __ldg(hp + l3.stride);
+  h.hz = __ldg(hp + 2 * l3.stride);
+#pragma unroll
+  for (int c = 0; c < 6; ++c) h.hc[c] = __ldg(cp + c * l6.stride);
+}
+
+// Run one track (p, C in registers) through layers 0..L-1; the next layer's
+// hit is loaded while the current layer computes.  Returns the OR of the
+// per-layer status bits.
+template <int VARIANT>
+__device__ __forceinline__ unsigned chain_track(float (&p)[6], float (&C)[21], float qf, float bz,
+                                                int L, const int32_t *kinds, const float *pos,
+                                                const float *hits, int64_t hit_stride,
+                                                const float *hitcovs, int64_t hc_stride,
+                                                const ChainLoc &l3, const ChainLoc &l6) {
+  unsigned st = 0;
+  LayerHit next;
+  load_layer_hit(hits, hit_stride, hitcovs, hc_stride, 0, l3, l6, next);
+  for (int l = 0; l < L; ++l) {
+    const LayerHit h = next;
+    if (l + 1 < L) load_layer_hit(hits, hit_stride, hitcovs, hc_stride, l + 1, l3, l6, next);
+    if (kinds[l] == kP2z)
+      st |= p2z_step<VARIANT>(p, C, qf, bz, pos[l], h.hx, h.hy, h.hc[0], h.hc[1], h.hc[2]);
+    else
+      st |= p2r_step<VARIANT>(p, C, qf, bz, pos[l], h.hx, h.hy, h.hz, h.hc);
+  }
+  return st;
+}
+
+}  // namespace kf

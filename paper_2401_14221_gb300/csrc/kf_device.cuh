@@ -62,6 +62,17 @@ constexpr uint64_t kP2rNZ =
     bit(4, 0) | bit(4, 1) | bit(4, 3) | bit(4, 4) |
     bit(5, 5);
 constexpr uint64_t kP2rOne = bit(2, 2) | bit(3, 3) | bit(5, 5);
+// p2r in the surface frame at the crossing point, rows (t, r, z', k, phi', theta):
+// t is the tangential and r the radial position coordinate.  The radial row
+// n.J is identically zero (the crossing stays on the cylinder), so it is
+// structurally zero here and C' has an exactly zero radial row and column.
+constexpr uint64_t kP2rFrameNZ =
+    bit(0, 0) | bit(0, 1) | bit(0, 3) | bit(0, 4) |
+    bit(2, 0) | bit(2, 1) | bit(2, 2) | bit(2, 3) | bit(2, 4) | bit(2, 5) |
+    bit(3, 3) |
+    bit(4, 0) | bit(4, 1) | bit(4, 3) | bit(4, 4) |
+    bit(5, 5);
+constexpr uint64_t kP2rFrameOne = bit(2, 2) | bit(3, 3) | bit(5, 5);
 
 // Azimuth wrapped to (-pi, pi]: subtract the nearest multiple of 2 pi in two
 // parts (float(2 pi) and its remainder), so the wrap adds < 1e-13 error.
@@ -287,21 +298,22 @@ __device__ __forceinline__ bool propagate_to_r(const float (&in)[6], float qf, f
 // ---------------------------------------------------------------- update
 // Update variants.
 enum Variant : int { kFP32 = 0, kFP64Update = 1, kJoseph = 2 };
-// Measurement models.
+// Step kinds.
 enum Kind : int { kP2z = 0, kP2r = 1 };
 
-// Two-row Kalman update given U = C' H^T (columns U0, U1), the innovation
-// covariance S = H U + V, V itself and the residual r.  The first
-// measurement row is H0 = (h0x, h0y) on (x, y); the second is e_y (p2z) or
-// e_z (p2r).  For p2z the z row/column of C' is structurally zero, so its
-// gain row is skipped and stays zero.  Returns kSNotPD (state untouched) or 0.
-template <int VARIANT, int KIND>
+// Two-row Kalman update in a frame where the measurement is
+//   row 0: h0 * (component 0),   row 1: component M1,
+// and component SKIP has a structurally zero row and column in C' (the
+// surface normal: z for p2z, the radial coordinate for p2r in the surface
+// frame), so its gain row is skipped and stays zero.  U = C' H^T (columns
+// U0, U1), S = H U + V, r the residual.  Returns kSNotPD (state untouched)
+// or 0.
+template <int VARIANT, int SKIP, int M1>
 __device__ __forceinline__ unsigned kalman_update(float (&p)[6], float (&C)[21],
                                                   const float (&U0)[6], const float (&U1)[6],
-                                                  float S00, float S01, float S11, float h0x,
-                                                  float h0y, float V00, float V01, float V11,
-                                                  float r0, float r1) {
-  constexpr bool kSkipZ = (KIND == kP2z);
+                                                  float S00, float S01, float S11, float h0,
+                                                  float V00, float V01, float V11, float r0,
+                                                  float r1) {
   if constexpr (VARIANT == kFP64Update) {
     // S^-1, K and C'' = C' - K U^T in double precision.
     const double dS00 = S00, dS01 = S01, dS11 = S11;
@@ -312,89 +324,111 @@ __device__ __forceinline__ unsigned kalman_update(float (&p)[6], float (&C)[21],
     double K0[6], K1[6];
 #pragma unroll
     for (int i = 0; i < 6; ++i) {
-      if (kSkipZ && i == 2) continue;
+      if (i == SKIP) continue;
       K0[i] = (double)U0[i] * Si00 + (double)U1[i] * Si01;
       K1[i] = (double)U0[i] * Si01 + (double)U1[i] * Si11;
       p[i] = (float)((double)p[i] + K0[i] * (double)r0 + K1[i] * (double)r1);
     }
+    // G = S^-1 V; columns of a measured component use the cancellation-free
+    // form (see the FP32 branch below).
+    const double G00 = Si00 * V00 + Si01 * V01, G01 = Si00 * V01 + Si01 * V11;
+    const double G10 = Si01 * V00 + Si11 * V01, G11 = Si01 * V01 + Si11 * V11;
+    const double ih0 = 1.0 / (double)h0;
 #pragma unroll
     for (int i = 0; i < 6; ++i) {
-      if (kSkipZ && i == 2) continue;
+      if (i == SKIP) continue;
 #pragma unroll
       for (int m = 0; m <= i; ++m) {
-        if (kSkipZ && m == 2) continue;
-        C[tri(i, m)] = (float)((double)C[tri(i, m)] -
-                               (K0[i] * (double)U0[m] + K1[i] * (double)U1[m]));
+        if (m == SKIP) continue;
+        const bool im = (i == 0 || i == M1), mm = (m == 0 || m == M1);
+        double v;
+        if (mm || im) {
+          const int r = mm ? i : m, c = mm ? m : i;  // row r, measured column c
+          v = (c == 0) ? ((double)U0[r] * G00 + (double)U1[r] * G10) * ih0
+                       : (double)U0[r] * G01 + (double)U1[r] * G11;
+        } else {
+          v = (double)C[tri(i, m)] - (K0[i] * (double)U0[m] + K1[i] * (double)U1[m]);
+        }
+        C[tri(i, m)] = (float)v;
       }
     }
     return 0u;
   } else {
-  const float det = fmaf(S00, S11, -S01 * S01);
-  if (!(S00 > 0.0f) || !(det > 0.0f)) return kSNotPD;
-  const float inv = 1.0f / det;
-  const float Si00 = S11 * inv, Si01 = -S01 * inv, Si11 = S00 * inv;
-  float K0[6], K1[6];
-#pragma unroll
-  for (int i = 0; i < 6; ++i) {
-    if (kSkipZ && i == 2) {
-      K0[i] = K1[i] = 0.0f;
-      continue;
-    }
-    K0[i] = fmaf(U0[i], Si00, U1[i] * Si01);
-    K1[i] = fmaf(U0[i], Si01, U1[i] * Si11);
-    p[i] = fmaf(K0[i], r0, fmaf(K1[i], r1, p[i]));
-  }
-
-  if constexpr (VARIANT == kJoseph) {
-    // Product (Joseph) form: B = (I - K H) C' = C' - K U^T, then
-    // C'' = B (I - K H)^T + K V K^T = B - (B H0^T) K0^T - (B H1^T) K1^T + K V K^T,
-    // a sum of positive semi-definite terms for any gain K.
-    float B[6][6];
-#pragma unroll
-    for (int i = 0; i < 6; ++i)
-#pragma unroll
-      for (int j = 0; j < 6; ++j)
-        B[i][j] = C[tri(i, j)] - fmaf(K0[i], U0[j], K1[i] * U1[j]);
-    float b0[6], b1[6];
+    const float det = fmaf(S00, S11, -S01 * S01);
+    if (!(S00 > 0.0f) || !(det > 0.0f)) return kSNotPD;
+    const float inv = 1.0f / det;
+    const float Si00 = S11 * inv, Si01 = -S01 * inv, Si11 = S00 * inv;
+    float K0[6], K1[6];
 #pragma unroll
     for (int i = 0; i < 6; ++i) {
-      b0[i] = fmaf(h0x, B[i][0], h0y * B[i][1]);
-      b1[i] = (KIND == kP2z) ? B[i][1] : B[i][2];
-    }
-#pragma unroll
-    for (int i = 0; i < 6; ++i) {
-      if (kSkipZ && i == 2) continue;
-      const float kv0 = fmaf(K0[i], V00, K1[i] * V01);
-      const float kv1 = fmaf(K0[i], V01, K1[i] * V11);
-#pragma unroll
-      for (int m = 0; m <= i; ++m) {
-        if (kSkipZ && m == 2) continue;
-        float c = B[i][m];
-        c = fmaf(-b0[i], K0[m], c);
-        c = fmaf(-b1[i], K1[m], c);
-        c = fmaf(kv0, K0[m], c);
-        c = fmaf(kv1, K1[m], c);
-        C[tri(i, m)] = c;
+      if (i == SKIP) {
+        K0[i] = K1[i] = 0.0f;
+        continue;
       }
+      K0[i] = fmaf(U0[i], Si00, U1[i] * Si01);
+      K1[i] = fmaf(U0[i], Si01, U1[i] * Si11);
+      p[i] = fmaf(K0[i], r0, fmaf(K1[i], r1, p[i]));
     }
-    return 0u;
-  } else {
+    if constexpr (VARIANT == kJoseph) {
+      // Product (Joseph) form: B = (I - K H) C' = C' - K U^T, then
+      // C'' = B (I - K H)^T + K V K^T = B - (B H0^T) K0^T - (B H1^T) K1^T + K V K^T,
+      // a sum of positive semi-definite terms for any gain K.
+      float B[6][6];
 #pragma unroll
-  for (int i = 0; i < 6; ++i) {
-    if (kSkipZ && i == 2) continue;
+      for (int i = 0; i < 6; ++i)
 #pragma unroll
-    for (int m = 0; m <= i; ++m) {
-      if (kSkipZ && m == 2) continue;
-      C[tri(i, m)] = C[tri(i, m)] - fmaf(K0[i], U0[m], K1[i] * U1[m]);
+        for (int j = 0; j < 6; ++j)
+          B[i][j] = C[tri(i, j)] - fmaf(K0[i], U0[j], K1[i] * U1[j]);
+      float b0[6], b1[6];
+#pragma unroll
+      for (int i = 0; i < 6; ++i) {
+        b0[i] = h0 * B[i][0];
+        b1[i] = B[i][M1];
+      }
+#pragma unroll
+      for (int i = 0; i < 6; ++i) {
+        if (i == SKIP) continue;
+        const float kv0 = fmaf(K0[i], V00, K1[i] * V01);
+        const float kv1 = fmaf(K0[i], V01, K1[i] * V11);
+#pragma unroll
+        for (int m = 0; m <= i; ++m) {
+          if (m == SKIP) continue;
+          float c = B[i][m];
+          c = fmaf(-b0[i], K0[m], c);
+          c = fmaf(-b1[i], K1[m], c);
+          c = fmaf(kv0, K0[m], c);
+          c = fmaf(kv1, K1[m], c);
+          C[tri(i, m)] = c;
+        }
+      }
+      return 0u;
+    } else {
+      // Standard form C'' = C' - K U^T, except where a measured component
+      // (0 or M1) is involved: there C' - K U^T = C' H^T S^-1 V H^-T exactly
+      // (because I - S^-1 (S - V) = S^-1 V), with no subtraction.  A precise
+      // hit shrinks the measured variances by orders of magnitude; in the
+      // subtracted form those digits would cancel away.
+      const float G00 = fmaf(Si00, V00, Si01 * V01), G01 = fmaf(Si00, V01, Si01 * V11);
+      const float G10 = fmaf(Si01, V00, Si11 * V01), G11 = fmaf(Si01, V01, Si11 * V11);
+      const float ih0 = 1.0f / h0;
+#pragma unroll
+      for (int i = 0; i < 6; ++i) {
+        if (i == SKIP) continue;
+#pragma unroll
+        for (int m = 0; m <= i; ++m) {
+          if (m == SKIP) continue;
+          const bool im = (i == 0 || i == M1), mm = (m == 0 || m == M1);
+          if (mm || im) {
+            const int r = mm ? i : m, c = mm ? m : i;  // row r, measured column c
+            C[tri(i, m)] = (c == 0) ? fmaf(U0[r], G00, U1[r] * G10) * ih0
+                                    : fmaf(U0[r], G01, U1[r] * G11);
+          } else {
+            C[tri(i, m)] = C[tri(i, m)] - fmaf(K0[i], U0[m], K1[i] * U1[m]);
+          }
+        }
+      }
+      return 0u;
     }
-  }
-  (void)h0x;
-  (void)h0y;
-  (void)V00;
-  (void)V01;
-  (void)V11;
-  return 0u;
-  }
   }
 }
 
@@ -407,7 +441,7 @@ __device__ __forceinline__ unsigned p2z_step(float (&p)[6], float (&C)[21], floa
   float pp[6], J[36], Cp[21];
   if (!propagate_to_z(p, qf, bz, zt, pp, J)) return kNoIntersect;
   transport<kP2zNZ, kP2zOne>(J, C, Cp);
-  // H = [e_x; e_y]: U = columns x and y of C'.
+  // H = [e_x; e_y]: U = columns x and y of C' (its z row and column are zero).
   float U0[6], U1[6];
 #pragma unroll
   for (int i = 0; i < 6; ++i) {
@@ -415,8 +449,8 @@ __device__ __forceinline__ unsigned p2z_step(float (&p)[6], float (&C)[21], floa
     U1[i] = Cp[tri(i, 1)];
   }
   const float S00 = U0[0] + vxx, S01 = U0[1] + vxy, S11 = U1[1] + vyy;
-  const unsigned st = kalman_update<VARIANT, kP2z>(pp, Cp, U0, U1, S00, S01, S11, 1.0f, 0.0f,
-                                                   vxx, vxy, vyy, hx - pp[0], hy - pp[1]);
+  const unsigned st = kalman_update<VARIANT, 2, 1>(pp, Cp, U0, U1, S00, S01, S11, 1.0f, vxx,
+                                                   vxy, vyy, hx - pp[0], hy - pp[1]);
 #pragma unroll
   for (int i = 0; i < 6; ++i) p[i] = pp[i];
 #pragma unroll
@@ -426,37 +460,71 @@ __device__ __forceinline__ unsigned p2z_step(float (&p)[6], float (&C)[21], floa
 }
 
 // One p2r step on registers.  hc = packed 3x3 hit covariance.
+//
+// The covariance is transported and updated in the surface frame at the
+// crossing point P' = R (cos a, sin a): position coordinates t (along
+// (-sin a, cos a)) and r (along (cos a, sin a)).  The radial row of the
+// Jacobian is identically zero, so C' has an exactly zero radial row and
+// column there; rotating the updated covariance back gives
+// C_xx = sin^2 a C_tt, C_xy = -sin a cos a C_tt, ..., which keeps full
+// relative precision even where an axis is nearly radial (in Cartesian FP32,
+// C_xx would be a difference of much larger terms).
 template <int VARIANT>
 __device__ __forceinline__ unsigned p2r_step(float (&p)[6], float (&C)[21], float qf, float bz,
                                              float R, float hx, float hy, float hz,
                                              const float (&hc)[6]) {
   float pp[6], J[36], Cp[21];
   if (!propagate_to_r(p, qf, bz, R, pp, J)) return kNoIntersect;
-  transport<kP2rNZ, kP2rOne>(J, C, Cp);
-  // Measurement direction at the hit: u = (-sin phi_h, cos phi_h), and z.
+  const float ip = rsqrtf(fmaf(pp[0], pp[0], pp[1] * pp[1]));
+  const float ca = pp[0] * ip, sa = pp[1] * ip;  // direction of P'
+#pragma unroll
+  for (int j = 0; j < 6; ++j) {
+    J[0 * 6 + j] = fmaf(-sa, J[0 * 6 + j], ca * J[1 * 6 + j]);  // t row
+    J[1 * 6 + j] = 0.0f;                                      // r row: zero
+  }
+  transport<kP2rFrameNZ, kP2rFrameOne>(J, C, Cp);
+  // Measurement direction at the hit, u = (-sin phi_h, cos phi_h), and z.
+  // In the frame u acts on t with weight u.t = cos(phi_h - a) (the radial
+  // column of C' is zero).
   const float ir = rsqrtf(fmaf(hx, hx, hy * hy));
   const float ux = -hy * ir, uy = hx * ir;
+  const float ut = fmaf(-sa, ux, ca * uy);
   float U0[6], U1[6];
 #pragma unroll
   for (int i = 0; i < 6; ++i) {
-    U0[i] = fmaf(ux, Cp[tri(i, 0)], uy * Cp[tri(i, 1)]);
+    U0[i] = ut * Cp[tri(i, 0)];
     U1[i] = Cp[tri(i, 2)];
   }
   // V = P V_hit P^T with P = [[ux, uy, 0], [0, 0, 1]].
   const float V00 = fmaf(ux * ux, hc[0], fmaf(2.0f * ux * uy, hc[1], uy * uy * hc[2]));
   const float V01 = fmaf(ux, hc[3], uy * hc[4]);
   const float V11 = hc[5];
-  const float S00 = fmaf(ux, U0[0], fmaf(uy, U0[1], V00));
+  const float S00 = fmaf(ut, U0[0], V00);
   const float S01 = U0[2] + V01;
   const float S11 = U1[2] + V11;
   const float r0 = fmaf(ux, hx - pp[0], uy * (hy - pp[1]));
   const float r1 = hz - pp[2];
-  const unsigned st = kalman_update<VARIANT, kP2r>(pp, Cp, U0, U1, S00, S01, S11, ux, uy, V00,
+  // frame state: the position offsets (t, r) start at 0 on P'
+  float pf[6] = {0.0f, 0.0f, pp[2], pp[3], pp[4], pp[5]};
+  const unsigned st = kalman_update<VARIANT, 1, 2>(pf, Cp, U0, U1, S00, S01, S11, ut, V00,
                                                    V01, V11, r0, r1);
+  p[0] = fmaf(-sa, pf[0], pp[0]);
+  p[1] = fmaf(ca, pf[0], pp[1]);
 #pragma unroll
-  for (int i = 0; i < 6; ++i) p[i] = pp[i];
+  for (int i = 2; i < 6; ++i) p[i] = pf[i];
+  // back to (x, y): only the t row/column carries position variance
+  const float ctt = Cp[tri(0, 0)];
+  C[tri(0, 0)] = sa * sa * ctt;
+  C[tri(1, 0)] = -sa * ca * ctt;
+  C[tri(1, 1)] = ca * ca * ctt;
 #pragma unroll
-  for (int e = 0; e < 21; ++e) C[e] = Cp[e];
+  for (int j = 2; j < 6; ++j) {
+    const float ctj = Cp[tri(j, 0)];
+    C[tri(j, 0)] = -sa * ctj;
+    C[tri(j, 1)] = ca * ctj;
+#pragma unroll
+    for (int m = 2; m <= j; ++m) C[tri(j, m)] = Cp[tri(j, m)];
+  }
   if (!st) p[4] = wrap_phi(p[4]);
   return st | (p[3] > 0.0f ? 0u : kBadK);
 }

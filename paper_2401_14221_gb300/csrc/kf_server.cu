@@ -1,0 +1,613 @@
+// kf_server.cu -- continuous-batching serving loop for the multi-layer chain.
+//
+// Events (a batch of tracks each, with a hit per layer) are submitted from
+// host threads at any time.  A scheduler thread owned by the server
+//
+//   1. admits pending events while an event slot and space in the caller's
+//      device arena are free, and copies each admitted event in on the
+//      copy-in stream;
+//   2. whenever no batch is computing, launches ONE batched chain kernel over
+//      every admitted event whose copies have landed (up to 128 events), on
+//      the compute stream -- events that arrived while the previous batch was
+//      running join the next batch, so work from different requests overlaps
+//      on the device;
+//   3. when a batch finishes, copies each event's results out on the
+//      copy-out stream while the next batch computes, and when those copies
+//      land marks the event done, records its latency (submit to results in
+//      host memory) and returns its slot and arena space.
+//
+// The track arithmetic is the chain kernel's (kf_chain.cuh), one thread per
+// track, so an event's results do not depend on what else is in its batch.
+// Streams, events and the thread are created when the server is created;
+// per-event device memory comes from the caller's arena (first-fit free list),
+// so submitting and serving allocate nothing.
+#include <algorithm>
+#include <chrono>
+#include <condition_variable>
+#include <deque>
+#include <map>
+#include <mutex>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "kf_chain.cuh"
+#include "kf_common.cuh"
+#include "kf_device.cuh"
+#include "kf_step.cuh"
+
+namespace kf {
+namespace srv {
+
+constexpr int kMaxBatch = 128;
+
+struct EventDesc {
+  float *state;
+  float *cov;
+  const int8_t *charge;
+  const float *hits;
+  const float *hitcovs;
+  uint8_t *status;
+  int64_t n;
+  int64_t block_begin;  // first block of this event in the batch grid
+};
+
+struct BatchArgs {
+  int32_t nev;
+  int32_t L;
+  float bz;
+  int32_t pad;
+  int32_t kinds[KF_MAX_LAYERS];
+  float pos[KF_MAX_LAYERS];
+  EventDesc ev[kMaxBatch];
+};
+
+// One grid over all tracks of a batch: block b belongs to the last event
+// whose block_begin <= b (binary search, uniform within the block).  Each
+// event's arrays are SoA [C][n_event].
+template <int VARIANT>
+__global__ void __launch_bounds__(256) batch_chain_kernel(const __grid_constant__ BatchArgs a) {
+  int lo = 0, hi = a.nev - 1;
+  const int64_t b = blockIdx.x;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (a.ev[mid].block_begin <= b) lo = mid;
+    else hi = mid - 1;
+  }
+  const EventDesc &e = a.ev[lo];
+  const int64_t i = (b - e.block_begin) * blockDim.x + threadIdx.x;
+  if (i >= e.n) return;
+  const ChainLoc l6{i, e.n}, l21{i, e.n}, l3{i, e.n};
+  float p[6], C[21];
+#pragma unroll
+  for (int c = 0; c < 6; ++c) p[c] = e.state[l6.base + c * l6.stride];
+#pragma unroll
+  for (int k = 0; k < 21; ++k) C[k] = e.cov[l21.base + k * l21.stride];
+  const float qf = (float)__ldg(e.charge + i);
+  unsigned st = chain_track<VARIANT>(p, C, qf, a.bz, a.L, a.kinds, a.pos, e.hits, 3 * e.n,
+                                     e.hitcovs, 6 * e.n, l3, l6);
+  st |= finite_status(p, C);
+#pragma unroll
+  for (int c = 0; c < 6; ++c) e.state[l6.base + c * l6.stride] = p[c];
+#pragma unroll
+  for (int k = 0; k < 21; ++k) e.cov[l21.base + k * l21.stride] = C[k];
+  if (e.status) e.status[i] = (uint8_t)st;
+}
+
+int64_t align256(int64_t x) { return (x + 255) & ~int64_t(255); }
+
+struct Layout {
+  int64_t state, cov, charge, hits, hitcovs, status, bytes;
+};
+
+Layout event_layout(int64_t n, int L) {
+  Layout l{};
+  int64_t off = 0;
+  l.state = off; off += align256(4 * 6 * n);
+  l.cov = off; off += align256(4 * 21 * n);
+  l.charge = off; off += align256(n);
+  l.hits = off; off += align256(4 * 3 * n * L);
+  l.hitcovs = off; off += align256(4 * 6 * n * L);
+  l.status = off; off += align256(n);
+  l.bytes = off;
+  return l;
+}
+
+enum class Phase { kPending, kCopying, kRunning, kReturning, kDone };
+
+struct Request {
+  uint64_t ticket;
+  int64_t n;
+  const float *state;
+  const float *cov;
+  const int8_t *charge;
+  const float *hits;
+  const float *hitcovs;
+  float *state_out;
+  float *cov_out;
+  uint8_t *status_out;
+  Phase phase = Phase::kPending;
+  int64_t off = -1;  // arena offset
+  Layout lay{};
+  cudaEvent_t ev = nullptr;  // copies in / copies out landed
+  std::chrono::steady_clock::time_point t_submit, t_done;
+};
+
+// First-fit allocator over [0, size) with coalescing.
+struct Arena {
+  std::map<int64_t, int64_t> free_;  // offset -> size
+  explicit Arena(int64_t size) { if (size > 0) free_[0] = size; }
+  int64_t alloc(int64_t bytes) {
+    for (auto it = free_.begin(); it != free_.end(); ++it) {
+      if (it->second >= bytes) {
+        const int64_t off = it->first, rest = it->second - bytes;
+        free_.erase(it);
+        if (rest > 0) free_[off + bytes] = rest;
+        return off;
+      }
+    }
+    return -1;
+  }
+  void release(int64_t off, int64_t bytes) {
+    auto it = free_.emplace(off, bytes).first;
+    auto nx = std::next(it);
+    if (nx != free_.end() && it->first + it->second == nx->first) {
+      it->second += nx->second;
+      free_.erase(nx);
+    }
+    if (it != free_.begin()) {
+      auto pv = std::prev(it);
+      if (pv->first + pv->second == it->first) {
+        pv->second += it->second;
+        free_.erase(it);
+      }
+    }
+  }
+};
+
+}  // namespace srv
+}  // namespace kf
+
+struct kf_server {
+  kf_server_config cfg;
+  char *arena_base = nullptr;
+  kf::srv::Arena arena{0};
+  std::mutex mu;
+  std::condition_variable cv_work, cv_done;
+  std::thread thread;
+  bool stop = false;
+  bool paused = false;
+  int error = KF_OK;
+  char error_msg[256] = "";
+  uint64_t next_ticket = 1;
+  std::deque<kf::srv::Request *> pending;
+  std::vector<kf::srv::Request *> copying, running, returning;
+  std::unordered_map<uint64_t, kf::srv::Request *> by_ticket;
+  std::vector<cudaEvent_t> event_pool;
+  cudaStream_t s_in = nullptr, s_compute = nullptr, s_out = nullptr;
+  cudaEvent_t batch_ev = nullptr;
+  bool batch_in_flight = false;
+  int in_flight = 0;  // admitted, not yet done
+  // statistics
+  std::vector<double> latencies_ms;
+  int64_t tracks_done = 0, batches = 0, max_batch_events = 0;
+};
+
+namespace {
+
+using kf::srv::Phase;
+using kf::srv::Request;
+
+void fail_locked(kf_server *s, cudaError_t e, const char *what) {
+  if (s->error == KF_OK) {
+    s->error = KF_ERR_CUDA;
+    snprintf(s->error_msg, sizeof(s->error_msg), "%s: %s", what, cudaGetErrorString(e));
+  }
+}
+
+// Copy an admitted request's inputs into its arena block (copy-in stream).
+bool start_copy_in(kf_server *s, Request *r) {
+  char *b = s->arena_base + r->off;
+  const int64_t n = r->n, L = s->cfg.L;
+  cudaError_t e = cudaMemcpyAsync(b + r->lay.state, r->state, 4 * 6 * n, cudaMemcpyDefault, s->s_in);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(b + r->lay.cov, r->cov, 4 * 21 * n, cudaMemcpyDefault, s->s_in);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(b + r->lay.charge, r->charge, n, cudaMemcpyDefault, s->s_in);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(b + r->lay.hits, r->hits, 4 * 3 * n * L, cudaMemcpyDefault, s->s_in);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(b + r->lay.hitcovs, r->hitcovs, 4 * 6 * n * L, cudaMemcpyDefault, s->s_in);
+  if (e == cudaSuccess) e = cudaEventRecord(r->ev, s->s_in);
+  if (e != cudaSuccess) {
+    fail_locked(s, e, "server copy in");
+    return false;
+  }
+  return true;
+}
+
+bool start_copy_out(kf_server *s, Request *r) {
+  char *b = s->arena_base + r->off;
+  const int64_t n = r->n;
+  cudaError_t e = cudaStreamWaitEvent(s->s_out, s->batch_ev, 0);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(r->state_out, b + r->lay.state, 4 * 6 * n, cudaMemcpyDefault, s->s_out);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(r->cov_out, b + r->lay.cov, 4 * 21 * n, cudaMemcpyDefault, s->s_out);
+  if (e == cudaSuccess && r->status_out)
+    e = cudaMemcpyAsync(r->status_out, b + r->lay.status, n, cudaMemcpyDefault, s->s_out);
+  if (e == cudaSuccess) e = cudaEventRecord(r->ev, s->s_out);
+  if (e != cudaSuccess) {
+    fail_locked(s, e, "server copy out");
+    return false;
+  }
+  return true;
+}
+
+bool launch_batch(kf_server *s, std::vector<Request *> &batch) {
+  using namespace kf;
+  using namespace kf::srv;
+  BatchArgs a{};
+  a.nev = (int32_t)batch.size();
+  a.L = s->cfg.L;
+  a.bz = s->cfg.bz;
+  for (int l = 0; l < s->cfg.L; ++l) {
+    a.kinds[l] = s->cfg.layers[l].kind;
+    a.pos[l] = s->cfg.layers[l].pos;
+  }
+  int64_t blocks = 0;
+  for (size_t k = 0; k < batch.size(); ++k) {
+    Request *r = batch[k];
+    char *b = s->arena_base + r->off;
+    EventDesc &e = a.ev[k];
+    e.state = reinterpret_cast<float *>(b + r->lay.state);
+    e.cov = reinterpret_cast<float *>(b + r->lay.cov);
+    e.charge = reinterpret_cast<const int8_t *>(b + r->lay.charge);
+    e.hits = reinterpret_cast<const float *>(b + r->lay.hits);
+    e.hitcovs = reinterpret_cast<const float *>(b + r->lay.hitcovs);
+    e.status = reinterpret_cast<uint8_t *>(b + r->lay.status);
+    e.n = r->n;
+    e.block_begin = blocks;
+    blocks += (r->n + 255) / 256;
+  }
+  cudaError_t e = cudaSuccess;
+  for (Request *r : batch) {
+    e = cudaStreamWaitEvent(s->s_compute, r->ev, 0);
+    if (e != cudaSuccess) break;
+  }
+  if (e == cudaSuccess && blocks > 0) {
+    const unsigned g = (unsigned)blocks;
+    switch (s->cfg.precision) {
+      case KF_FP32: batch_chain_kernel<kFP32><<<g, 256, 0, s->s_compute>>>(a); break;
+      case KF_FP64_UPDATE: batch_chain_kernel<kFP64Update><<<g, 256, 0, s->s_compute>>>(a); break;
+      default: batch_chain_kernel<kJoseph><<<g, 256, 0, s->s_compute>>>(a); break;
+    }
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaEventRecord(s->batch_ev, s->s_compute);
+  if (e != cudaSuccess) {
+    fail_locked(s, e, "server batch launch");
+    return false;
+  }
+  s->batches += 1;
+  s->max_batch_events = std::max<int64_t>(s->max_batch_events, (int64_t)batch.size());
+  return true;
+}
+
+// One pass of the scheduler; returns true if anything moved.
+bool schedule_once(kf_server *s) {
+  bool moved = false;
+  // copies out that landed: the event is done
+  for (size_t k = 0; k < s->returning.size();) {
+    Request *r = s->returning[k];
+    const cudaError_t q = cudaEventQuery(r->ev);
+    if (q == cudaErrorNotReady) {
+      ++k;
+      continue;
+    }
+    if (q != cudaSuccess) fail_locked(s, q, "server copy-out completion");
+    r->t_done = std::chrono::steady_clock::now();
+    r->phase = Phase::kDone;
+    s->latencies_ms.push_back(
+        std::chrono::duration<double, std::milli>(r->t_done - r->t_submit).count());
+    s->tracks_done += r->n;
+    s->arena.release(r->off, r->lay.bytes);
+    s->event_pool.push_back(r->ev);
+    r->ev = nullptr;
+    s->in_flight -= 1;
+    s->returning.erase(s->returning.begin() + k);
+    moved = true;
+    s->cv_done.notify_all();
+  }
+  // the running batch finished: copy its events out
+  if (s->batch_in_flight) {
+    const cudaError_t q = cudaEventQuery(s->batch_ev);
+    if (q != cudaErrorNotReady) {
+      if (q != cudaSuccess) fail_locked(s, q, "server batch completion");
+      for (Request *r : s->running) {
+        if (start_copy_out(s, r)) {
+          r->phase = Phase::kReturning;
+          s->returning.push_back(r);
+        }
+      }
+      s->running.clear();
+      s->batch_in_flight = false;
+      moved = true;
+    }
+  }
+  if (s->paused || s->error != KF_OK) return moved;
+  // admit while a slot, an event object and arena space are free
+  while (!s->pending.empty() && s->in_flight < s->cfg.max_events_in_flight &&
+         !s->event_pool.empty()) {
+    Request *r = s->pending.front();
+    const int64_t off = s->arena.alloc(r->lay.bytes);
+    if (off < 0) break;  // wait for space: first come, first served
+    r->off = off;
+    r->ev = s->event_pool.back();
+    s->event_pool.pop_back();
+    s->pending.pop_front();
+    s->in_flight += 1;
+    if (!start_copy_in(s, r)) break;
+    r->phase = Phase::kCopying;
+    s->copying.push_back(r);
+    moved = true;
+  }
+  // launch everything whose copies have landed
+  if (!s->batch_in_flight && !s->copying.empty()) {
+    std::vector<Request *> batch;
+    for (size_t k = 0; k < s->copying.size() && (int)batch.size() < kf::srv::kMaxBatch;) {
+      Request *r = s->copying[k];
+      if (cudaEventQuery(r->ev) == cudaSuccess) {
+        batch.push_back(r);
+        s->copying.erase(s->copying.begin() + k);
+      } else {
+        ++k;
+      }
+    }
+    if (!batch.empty() && launch_batch(s, batch)) {
+      for (Request *r : batch) r->phase = Phase::kRunning;
+      s->running = batch;
+      s->batch_in_flight = true;
+      moved = true;
+    }
+  }
+  return moved;
+}
+
+void scheduler_main(kf_server *s) {
+  cudaSetDevice(s->cfg.device);
+  std::unique_lock<std::mutex> lock(s->mu);
+  while (!s->stop) {
+    const bool moved = schedule_once(s);
+    const bool busy = s->batch_in_flight || !s->copying.empty() || !s->returning.empty();
+    if (moved) continue;
+    if (busy) {
+      // GPU work in flight: poll its events again shortly
+      lock.unlock();
+      std::this_thread::sleep_for(std::chrono::microseconds(10));
+      lock.lock();
+    } else {
+      s->cv_work.wait_for(lock, std::chrono::milliseconds(5));
+    }
+  }
+}
+
+int server_error(kf_server *s) {
+  return kf::set_error(s->error, "server: %s", s->error_msg);
+}
+
+}  // namespace
+
+extern "C" int64_t kf_server_event_bytes(int64_t n, int32_t L) {
+  if (n < 0 || L < 0 || L > KF_MAX_LAYERS) return -1;
+  return kf::srv::event_layout(n, L).bytes;
+}
+
+extern "C" int kf_server_create(const kf_server_config *cfg, kf_server **out) {
+  using namespace kf;
+  clear_error();
+  if (!cfg || !out) return set_error(KF_ERR_ARG, "cfg or out is NULL");
+  *out = nullptr;
+  if (cfg->L < 1 || cfg->L > KF_MAX_LAYERS)
+    return set_error(KF_ERR_ARG, "L = %d not in [1, %d]", cfg->L, KF_MAX_LAYERS);
+  for (int l = 0; l < cfg->L; ++l)
+    if (cfg->layers[l].kind != KF_P2Z && cfg->layers[l].kind != KF_P2R)
+      return set_error(KF_ERR_ARG, "layers[%d].kind = %d", l, cfg->layers[l].kind);
+  if (cfg->precision < KF_FP32 || cfg->precision > KF_JOSEPH)
+    return set_error(KF_ERR_ARG, "unknown precision %d", cfg->precision);
+  if (cfg->max_events_in_flight < 1)
+    return set_error(KF_ERR_ARG, "max_events_in_flight must be >= 1");
+  if (reinterpret_cast<uintptr_t>(cfg->arena) & 255u)
+    return set_error(KF_ERR_ARG, "arena must be 256-byte aligned");
+  if (int rc = check_cuda(cudaSetDevice(cfg->device), "cudaSetDevice")) return rc;
+  if (int rc = check_device_range(cfg->arena, cfg->arena_bytes, "arena")) return rc;
+
+  kf_server *s = new kf_server;
+  s->cfg = *cfg;
+  s->arena_base = static_cast<char *>(cfg->arena);
+  s->arena = kf::srv::Arena(cfg->arena_bytes);
+  cudaError_t e = cudaStreamCreateWithFlags(&s->s_in, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->s_compute, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->s_out, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->batch_ev, cudaEventDisableTiming);
+  for (int k = 0; e == cudaSuccess && k < cfg->max_events_in_flight; ++k) {
+    cudaEvent_t ev;
+    e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+    if (e == cudaSuccess) s->event_pool.push_back(ev);
+  }
+  if (e != cudaSuccess) {
+    kf_server_destroy(s);
+    return check_cuda(e, "server create");
+  }
+  s->thread = std::thread(scheduler_main, s);
+  *out = s;
+  return KF_OK;
+}
+
+extern "C" int kf_server_submit(kf_server *s, int64_t n, const float *state, const float *cov,
+                                const int8_t *charge, const float *hits, const float *hit_covs,
+                                float *state_out, float *cov_out, uint8_t *status_out,
+                                uint64_t *ticket) {
+  using namespace kf;
+  clear_error();
+  if (!s || !ticket) return set_error(KF_ERR_ARG, "server or ticket is NULL");
+  if (n < 1) return set_error(KF_ERR_ARG, "an event needs n >= 1 tracks");
+  if (!state || !cov || !charge || !hits || !hit_covs || !state_out || !cov_out)
+    return set_error(KF_ERR_ARG, "a required pointer is NULL");
+  const kf::srv::Layout lay = kf::srv::event_layout(n, s->cfg.L);
+  if (lay.bytes > s->cfg.arena_bytes)
+    return set_error(KF_ERR_ARG, "event of %lld tracks needs %lld arena bytes, the arena has %lld",
+                     (long long)n, (long long)lay.bytes, (long long)s->cfg.arena_bytes);
+  Request *r = new Request;
+  r->n = n;
+  r->state = state;
+  r->cov = cov;
+  r->charge = charge;
+  r->hits = hits;
+  r->hitcovs = hit_covs;
+  r->state_out = state_out;
+  r->cov_out = cov_out;
+  r->status_out = status_out;
+  r->lay = lay;
+  r->t_submit = std::chrono::steady_clock::now();
+  {
+    std::lock_guard<std::mutex> lock(s->mu);
+    if (s->error != KF_OK) {
+      delete r;
+      return server_error(s);
+    }
+    r->ticket = s->next_ticket++;
+    s->pending.push_back(r);
+    s->by_ticket[r->ticket] = r;
+    *ticket = r->ticket;
+  }
+  s->cv_work.notify_one();
+  return KF_OK;
+}
+
+extern "C" int kf_server_poll(kf_server *s, uint64_t ticket, int32_t *done) {
+  using namespace kf;
+  clear_error();
+  if (!s || !done) return set_error(KF_ERR_ARG, "server or done is NULL");
+  std::lock_guard<std::mutex> lock(s->mu);
+  auto it = s->by_ticket.find(ticket);
+  if (it == s->by_ticket.end()) return set_error(KF_ERR_ARG, "unknown ticket %llu",
+                                                 (unsigned long long)ticket);
+  *done = it->second->phase == Phase::kDone ? 1 : 0;
+  if (s->error != KF_OK) return server_error(s);
+  return KF_OK;
+}
+
+extern "C" int kf_server_wait(kf_server *s, uint64_t ticket, double timeout_s) {
+  using namespace kf;
+  clear_error();
+  if (!s) return set_error(KF_ERR_ARG, "server is NULL");
+  std::unique_lock<std::mutex> lock(s->mu);
+  auto it = s->by_ticket.find(ticket);
+  if (it == s->by_ticket.end())
+    return set_error(KF_ERR_ARG, "unknown ticket %llu", (unsigned long long)ticket);
+  Request *r = it->second;
+  const auto deadline = std::chrono::steady_clock::now() +
+                        std::chrono::duration_cast<std::chrono::steady_clock::duration>(
+                            std::chrono::duration<double>(timeout_s > 0 ? timeout_s : 0.0));
+  while (r->phase != Phase::kDone && s->error == KF_OK) {
+    if (s->cv_done.wait_until(lock, deadline) == std::cv_status::timeout &&
+        r->phase != Phase::kDone)
+      return set_error(KF_ERR_TIMEOUT, "ticket %llu not done within %.3f s",
+                       (unsigned long long)ticket, timeout_s);
+  }
+  if (r->phase != Phase::kDone) return server_error(s);
+  s->by_ticket.erase(it);
+  delete r;
+  return KF_OK;
+}
+
+extern "C" int kf_server_pause(kf_server *s, int32_t paused) {
+  using namespace kf;
+  clear_error();
+  if (!s) return set_error(KF_ERR_ARG, "server is NULL");
+  {
+    std::lock_guard<std::mutex> lock(s->mu);
+    s->paused = paused != 0;
+  }
+  s->cv_work.notify_one();
+  return KF_OK;
+}
+
+extern "C" int kf_server_get_stats(kf_server *s, kf_server_stats *out) {
+  using namespace kf;
+  clear_error();
+  if (!s || !out) return set_error(KF_ERR_ARG, "server or out is NULL");
+  std::lock_guard<std::mutex> lock(s->mu);
+  std::vector<double> v = s->latencies_ms;
+  std::sort(v.begin(), v.end());
+  *out = kf_server_stats{};
+  out->events_done = (int64_t)v.size();
+  out->tracks_done = s->tracks_done;
+  out->batches = s->batches;
+  out->max_batch_events = s->max_batch_events;
+  if (!v.empty()) {
+    auto pct = [&](double q) { return v[std::min(v.size() - 1, (size_t)(q * (v.size() - 1) + 0.5))]; };
+    out->p50_ms = pct(0.50);
+    out->p99_ms = pct(0.99);
+    out->max_ms = v.back();
+    double sum = 0;
+    for (double x : v) sum += x;
+    out->mean_ms = sum / (double)v.size();
+  }
+  return KF_OK;
+}
+
+extern "C" int kf_server_reset_stats(kf_server *s) {
+  using namespace kf;
+  clear_error();
+  if (!s) return set_error(KF_ERR_ARG, "server is NULL");
+  std::lock_guard<std::mutex> lock(s->mu);
+  s->latencies_ms.clear();
+  s->tracks_done = s->batches = s->max_batch_events = 0;
+  return KF_OK;
+}
+
+extern "C" int kf_server_destroy(kf_server *s) {
+  using namespace kf;
+  clear_error();
+  if (!s) return KF_OK;
+  {
+    std::unique_lock<std::mutex> lock(s->mu);
+    s->paused = false;
+  }
+  s->cv_work.notify_one();
+  // let admitted work finish (bounded), then stop the thread
+  const auto deadline = std::chrono::steady_clock::now() + std::chrono::seconds(30);
+  for (;;) {
+    {
+      std::lock_guard<std::mutex> lock(s->mu);
+      if ((s->pending.empty() && s->in_flight == 0) || s->error != KF_OK ||
+          std::chrono::steady_clock::now() > deadline)
+        break;
+    }
+    std::this_thread::sleep_for(std::chrono::milliseconds(1));
+  }
+  {
+    std::lock_guard<std::mutex> lock(s->mu);
+    s->stop = true;
+  }
+  s->cv_work.notify_one();
+  if (s->thread.joinable()) s->thread.join();
+  if (s->s_in) cudaStreamSynchronize(s->s_in);
+  if (s->s_compute) cudaStreamSynchronize(s->s_compute);
+  if (s->s_out) cudaStreamSynchronize(s->s_out);
+  for (auto &kv : s->by_ticket) {
+    if (kv.second->ev) cudaEventDestroy(kv.second->ev);
+    delete kv.second;
+  }
+  for (cudaEvent_t ev : s->event_pool) cudaEventDestroy(ev);
+  if (s->batch_ev) cudaEventDestroy(s->batch_ev);
+  if (s->s_in) cudaStreamDestroy(s->s_in);
+  if (s->s_compute) cudaStreamDestroy(s->s_compute);
+  if (s->s_out) cudaStreamDestroy(s->s_out);
+  delete s;
+  return KF_OK;
+}

@@ -10,6 +10,8 @@
 // instructions.
 #include <cuda_runtime.h>
 
+#include <atomic>
+
 #include "kf_common.cuh"
 #include "kf_device.cuh"
 #include "kf_step.cuh"
@@ -113,8 +115,18 @@ static int launch_step(const kf_params *params, kf_layout layout, const float *s
   return launch_step_kernel(KIND, params->precision, a, static_cast<cudaStream_t>(stream));
 }
 
+namespace {
+std::atomic<int> g_step_mode{KF_STEP_AUTO};
+}
+
+int step_kernel_mode() { return g_step_mode.load(std::memory_order_relaxed); }
+
 int launch_step_kernel(int kind, int precision, const StepArgs &a, cudaStream_t s) {
   if (a.n == 0) return KF_OK;
+  // AoSoA tiles are contiguous runs: stage them with bulk copies unless the
+  // direct kernel was asked for.
+  if (!a.soa && step_kernel_mode() != KF_STEP_DIRECT)
+    return launch_step_staged(kind, precision, a, s);
   const int threads = 256;
   const int64_t blocks = (a.n + threads - 1) / threads;
   if (blocks > 0x7fffffffLL) return set_error(KF_ERR_ARG, "n too large for one launch");
@@ -155,4 +167,12 @@ extern "C" int kf_p2r_propagate_update(const kf_params *params, kf_layout layout
                                        uint8_t *status, void *stream) {
   return kf::launch_step<kf::kP2r>(params, layout, state_in, cov_in, state_out, cov_out, charge,
                                    hit, hit_cov, r_surf, surf_per_track, status, stream);
+}
+
+extern "C" int kf_set_step_kernel(int32_t mode) {
+  kf::clear_error();
+  if (mode != KF_STEP_AUTO && mode != KF_STEP_DIRECT && mode != KF_STEP_STAGED)
+    return kf::set_error(KF_ERR_ARG, "unknown step kernel mode %d", mode);
+  kf::g_step_mode.store(mode, std::memory_order_relaxed);
+  return KF_OK;
 }

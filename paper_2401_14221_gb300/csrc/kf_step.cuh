@@ -29,4 +29,10 @@ struct StepArgs {
 // with the given KF_FP32 / KF_FP64_UPDATE / KF_JOSEPH variant.
 int launch_step_kernel(int kind, int precision, const StepArgs &a, cudaStream_t s);
 
+// The persistent bulk-async-staged kernel (AoSoA layouts only).
+int launch_step_staged(int kind, int precision, const StepArgs &a, cudaStream_t s);
+
+// Process-wide choice between the kernels: KF_STEP_AUTO / _DIRECT / _STAGED.
+int step_kernel_mode();
+
 }  // namespace kf

@@ -1,0 +1,192 @@
+// kf_step_compressed.cu -- the single step on a compressed covariance store:
+// per track six FP32 standard deviations sigma_i = sqrt(C_ii) and fifteen
+// FP16 correlation coefficients rho_ij = C_ij / (sigma_i sigma_j)
+// (off-diagonal entries in packed order 10, 20, 21, 30, ..., 54).
+//
+// The step is HBM-bound, so a smaller covariance store is a direct speed-up:
+// 24 + 30 = 54 B instead of 84 B per covariance, 193 B instead of 253 B per
+// p2r track (read 115, write 78).  FP16 keeps correlations to 2^-12 absolute
+// (|rho| <= 1), i.e. every covariance element to ~2.4e-4 of its correlation
+// scale sqrt(C_ii C_jj), inside the 1e-3 element bound.  Arithmetic is
+// unchanged: the kernel decodes to FP32 registers, runs the same step and
+// encodes the result (round to nearest).  A track that is not propagated
+// (no intersection) gets its input sigma/rho back bit for bit.
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+
+#include "kf_common.cuh"
+#include "kf_device.cuh"
+#include "kf_step.cuh"
+
+namespace kf {
+namespace {
+
+struct CompressedArgs {
+  const float *state_in;
+  const float *sigma_in;
+  const __half *rho_in;
+  float *state_out;
+  float *sigma_out;
+  __half *rho_out;
+  const int8_t *charge;
+  const float *hit;
+  const float *hitcov;
+  const float *surf;
+  uint8_t *status;
+  int64_t n;
+  int32_t soa;
+  int32_t lw;
+  float bz;
+  int32_t surf_per_track;
+};
+
+struct Loc {
+  int64_t base;
+  int64_t stride;
+};
+
+template <int C>
+__device__ __forceinline__ Loc locate(int64_t i, int64_t n, int32_t soa, int32_t lw) {
+  if (soa) return {i, n};
+  const int64_t W = int64_t(1) << lw;
+  return {(i >> lw) * (C * W) + (i & (W - 1)), W};
+}
+
+// Off-diagonal (row, column) of correlation k, packed order.
+__device__ __forceinline__ constexpr int od_row(int k) {
+  return k < 1 ? 1 : k < 3 ? 2 : k < 6 ? 3 : k < 10 ? 4 : 5;
+}
+__device__ __forceinline__ constexpr int od_col(int k) {
+  return k - (od_row(k) * (od_row(k) - 1)) / 2;
+}
+
+template <int KIND, int VARIANT>
+__global__ void __launch_bounds__(256) step_compressed_kernel(const CompressedArgs a) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= a.n) return;
+  const Loc l6 = locate<6>(i, a.n, a.soa, a.lw);
+  const Loc l15 = locate<15>(i, a.n, a.soa, a.lw);
+  const Loc l3 = locate<3>(i, a.n, a.soa, a.lw);
+
+  float p[6], sg[6], C[21];
+  __half rh[15];
+#pragma unroll
+  for (int c = 0; c < 6; ++c) p[c] = __ldg(a.state_in + l6.base + c * l6.stride);
+#pragma unroll
+  for (int c = 0; c < 6; ++c) sg[c] = __ldg(a.sigma_in + l6.base + c * l6.stride);
+#pragma unroll
+  for (int k = 0; k < 15; ++k) rh[k] = a.rho_in[l15.base + k * l15.stride];
+  // decode: C_ii = sigma_i^2, C_ij = rho_ij sigma_i sigma_j
+#pragma unroll
+  for (int c = 0; c < 6; ++c) C[tri(c, c)] = sg[c] * sg[c];
+#pragma unroll
+  for (int k = 0; k < 15; ++k)
+    C[tri(od_row(k), od_col(k))] = __half2float(rh[k]) * sg[od_row(k)] * sg[od_col(k)];
+  const float qf = (float)__ldg(a.charge + i);
+  const float surf = __ldg(a.surf + (a.surf_per_track ? i : 0));
+
+  unsigned st;
+  if (KIND == kP2z) {
+    const float hx = __ldg(a.hit + l3.base);
+    const float hy = __ldg(a.hit + l3.base + l3.stride);
+    const float vxx = __ldg(a.hitcov + l6.base);
+    const float vxy = __ldg(a.hitcov + l6.base + l6.stride);
+    const float vyy = __ldg(a.hitcov + l6.base + 2 * l6.stride);
+    st = p2z_step<VARIANT>(p, C, qf, a.bz, surf, hx, hy, vxx, vxy, vyy);
+  } else {
+    const float hx = __ldg(a.hit + l3.base);
+    const float hy = __ldg(a.hit + l3.base + l3.stride);
+    const float hz = __ldg(a.hit + l3.base + 2 * l3.stride);
+    float hc[6];
+#pragma unroll
+    for (int c = 0; c < 6; ++c) hc[c] = __ldg(a.hitcov + l6.base + c * l6.stride);
+    st = p2r_step<VARIANT>(p, C, qf, a.bz, surf, hx, hy, hz, hc);
+  }
+  st |= finite_status(p, C);
+
+  if (!(st & kNoIntersect)) {
+    // encode: sigma_i = sqrt(C_ii), rho_ij = C_ij / (sigma_i sigma_j) in [-1, 1]
+    float inv[6];
+#pragma unroll
+    for (int c = 0; c < 6; ++c) {
+      sg[c] = sqrtf(fmaxf(C[tri(c, c)], 0.0f));
+      inv[c] = sg[c] > 0.0f ? 1.0f / sg[c] : 0.0f;
+    }
+#pragma unroll
+    for (int k = 0; k < 15; ++k) {
+      const float r = C[tri(od_row(k), od_col(k))] * inv[od_row(k)] * inv[od_col(k)];
+      rh[k] = __float2half_rn(fminf(fmaxf(r, -1.0f), 1.0f));
+    }
+  }
+#pragma unroll
+  for (int c = 0; c < 6; ++c) __stcs(a.state_out + l6.base + c * l6.stride, p[c]);
+#pragma unroll
+  for (int c = 0; c < 6; ++c) __stcs(a.sigma_out + l6.base + c * l6.stride, sg[c]);
+#pragma unroll
+  for (int k = 0; k < 15; ++k) a.rho_out[l15.base + k * l15.stride] = rh[k];
+  if (a.status) a.status[i] = (uint8_t)st;
+}
+
+}  // namespace
+}  // namespace kf
+
+extern "C" int kf_propagate_update_compressed(
+    int32_t kind, const kf_params *params, kf_layout layout, const float *state_in,
+    const float *sigma_in, const uint16_t *rho_in, float *state_out, float *sigma_out,
+    uint16_t *rho_out, const int8_t *charge, const float *hit, const float *hit_cov,
+    const float *surf, int32_t surf_per_track, uint8_t *status, void *stream) {
+  using namespace kf;
+  clear_error();
+  if (kind != KF_P2Z && kind != KF_P2R)
+    return set_error(KF_ERR_ARG, "kind = %d is neither KF_P2Z nor KF_P2R", kind);
+  if (!params) return set_error(KF_ERR_ARG, "params is NULL");
+  if (params->flags != 0) return set_error(KF_ERR_ARG, "params->flags must be 0");
+  if (params->precision < KF_FP32 || params->precision > KF_JOSEPH)
+    return set_error(KF_ERR_ARG, "unknown precision %d", params->precision);
+  LayoutDesc d;
+  if (int rc = check_layout(layout, &d)) return rc;
+  if (d.n == 0) return KF_OK;
+  if (surf_per_track != 0 && surf_per_track != 1)
+    return set_error(KF_ERR_ARG, "surf_per_track must be 0 or 1");
+  const void *fptrs[] = {state_in, sigma_in, rho_in, state_out, sigma_out, rho_out, hit, hit_cov};
+  for (const void *q : fptrs)
+    if (!aligned16(q)) return set_error(KF_ERR_ARG, "arrays must be 16-byte aligned");
+  const int64_t b6 = 4 * layout_floats(d, 6), b15 = 2 * layout_floats(d, 15);
+  const void *ptrs[] = {state_in, sigma_in, rho_in, state_out, sigma_out,
+                        rho_out,  charge,   hit,    hit_cov,   surf};
+  const int64_t bytes[] = {b6,  b6,  b15, b6, b6, b15, d.n, 4 * layout_floats(d, 3), b6,
+                           surf_per_track ? 4 * d.n : 4};
+  const char *names[] = {"state_in", "sigma_in", "rho_in", "state_out", "sigma_out",
+                         "rho_out",  "charge",   "hit",    "hit_cov",   "surf"};
+  for (int k = 0; k < 10; ++k)
+    if (int rc = check_device_range(ptrs[k], bytes[k], names[k])) return rc;
+  if (status)
+    if (int rc = check_device_range(status, d.n, "status")) return rc;
+  if (partial_overlap(state_in, b6, state_out, b6) || partial_overlap(sigma_in, b6, sigma_out, b6) ||
+      partial_overlap(rho_in, b15, rho_out, b15))
+    return set_error(KF_ERR_ARG, "input and output overlap without coinciding");
+
+  CompressedArgs a{state_in, sigma_in, reinterpret_cast<const __half *>(rho_in),
+                   state_out, sigma_out, reinterpret_cast<__half *>(rho_out),
+                   charge, hit, hit_cov, surf, status, d.n, d.soa, d.lw, params->bz,
+                   surf_per_track};
+  const int threads = 256;
+  const int64_t blocks = (d.n + threads - 1) / threads;
+  if (blocks > 0x7fffffffLL) return set_error(KF_ERR_ARG, "n too large for one launch");
+  const unsigned g = (unsigned)blocks;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (kind == KF_P2Z) {
+    switch (params->precision) {
+      case KF_FP32: step_compressed_kernel<kP2z, kFP32><<<g, threads, 0, s>>>(a); break;
+      case KF_FP64_UPDATE: step_compressed_kernel<kP2z, kFP64Update><<<g, threads, 0, s>>>(a); break;
+      default: step_compressed_kernel<kP2z, kJoseph><<<g, threads, 0, s>>>(a); break;
+    }
+  } else {
+    switch (params->precision) {
+      case KF_FP32: step_compressed_kernel<kP2r, kFP32><<<g, threads, 0, s>>>(a); break;
+      case KF_FP64_UPDATE: step_compressed_kernel<kP2r, kFP64Update><<<g, threads, 0, s>>>(a); break;
+      default: step_compressed_kernel<kP2r, kJoseph><<<g, threads, 0, s>>>(a); break;
+    }
+  }
+  return check_cuda(cudaGetLastError(), "compressed step launch");
+}

@@ -1,0 +1,296 @@
+// kf_step_staged.cu -- persistent single-step kernel with bulk-async staging
+// (paper section 2: propagateToZ / propagateToR + KalmanUpdate per track).
+//
+// The direct kernel (kf_step.cu) loads each track's 36 input floats with
+// scalar loads and then computes; a warp has nothing in flight while it
+// computes, so HBM idles unless many other warps happen to be loading.  Here
+// a persistent CTA splits the two jobs:
+//
+//   * one producer warp streams tiles of T = 256 tracks into shared memory
+//     with cp.async.bulk (the Blackwell bulk-copy engine), S = 3 stages deep,
+//     each completion tracked by an mbarrier's transaction count;
+//   * eight compute warps take a staged tile, read their track's inputs from
+//     shared memory (bank-conflict-free for AoSoA), release the stage, and run
+//     the step in registers, writing results straight to global memory.
+//
+// For AoSoA layouts a tile of an array is one contiguous run (T is a multiple
+// of the block width W), so a stage is four bulk copies.  charge and the
+// per-track surface are plain [n] arrays read directly (tiny, and a bulk copy
+// of a ragged tail could run past their end).  Every mbarrier wait is
+// bounded; on timeout the kernel records KF_DEVERR_TIMEOUT in a device error
+// word and leaves its loop, so a broken pipeline cannot hang the GPU.
+#include <cuda_runtime.h>
+
+#include <mutex>
+
+#include "kf_common.cuh"
+#include "kf_device.cuh"
+#include "kf_step.cuh"
+
+namespace kf {
+
+__device__ unsigned int g_device_error = 0;
+
+namespace staged {
+
+constexpr int kComputeWarps = 8;
+constexpr int kThreads = (kComputeWarps + 1) * 32;
+constexpr int kT = kComputeWarps * 32;  // tracks per tile
+constexpr int kStages = 3;
+constexpr int kStateB = kT * 6 * 4;
+constexpr int kCovB = kT * 21 * 4;
+constexpr int kHitB = kT * 3 * 4;
+constexpr int kHcB = kT * 6 * 4;
+constexpr int kStageB = kStateB + kCovB + kHitB + kHcB;
+constexpr int kSmemBytes = kStages * kStageB + 2 * kStages * 8;
+// Polls of a barrier before giving up (with back-off, several seconds).
+constexpr uint32_t kMaxPolls = 1u << 24;
+
+__device__ __forceinline__ uint32_t saddr(const void *p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(saddr(bar)), "r"(count)
+               : "memory");
+}
+
+__device__ __forceinline__ void mbar_fence_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes) {
+  uint64_t state;
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 %0, [%1], %2;"
+               : "=l"(state)
+               : "r"(saddr(bar)), "r"(bytes)
+               : "memory");
+  (void)state;
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+  uint64_t state;
+  asm volatile("mbarrier.arrive.shared::cta.b64 %0, [%1];"
+               : "=l"(state)
+               : "r"(saddr(bar))
+               : "memory");
+  (void)state;
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n"
+      " .reg .pred p;\n"
+      " mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n"
+      "}\n"
+      : "=r"(ok)
+      : "r"(saddr(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Wait for the phase with the given parity to complete; false on timeout.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
+  for (uint32_t it = 0; it < kMaxPolls; ++it) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if (it > 32) __nanosleep(128);
+  }
+  atomicOr(&g_device_error, (unsigned)KF_DEVERR_TIMEOUT);
+  return false;
+}
+
+// Global -> shared bulk copy completing on `bar` (sizes and addresses are
+// multiples of 16 bytes).
+__device__ __forceinline__ void bulk_g2s(void *sdst, const void *gsrc, uint32_t bytes,
+                                         uint64_t *bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
+          "r"(saddr(sdst)),
+      "l"(gsrc), "r"(bytes), "r"(saddr(bar))
+      : "memory");
+}
+
+template <int KIND, int VARIANT, int W>
+__global__ void __launch_bounds__(kThreads, 2) step_staged_kernel(const StepArgs a) {
+  static_assert(kT % W == 0, "tile must hold whole AoSoA blocks");
+  extern __shared__ __align__(128) unsigned char smem[];
+  uint64_t *full = reinterpret_cast<uint64_t *>(smem + kStages * kStageB);
+  uint64_t *empty = full + kStages;
+  const int warp = threadIdx.x >> 5;
+  const int lane = threadIdx.x & 31;
+  const int64_t ntiles = (a.n + kT - 1) / kT;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kStages; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], kComputeWarps);
+    }
+    mbar_fence_init();
+  }
+  __syncthreads();
+
+  if (warp == kComputeWarps) {
+    // ------------------------------------------------------------ producer
+    if (lane == 0) {
+      int k = 0;
+      for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x, ++k) {
+        const int s = k % kStages;
+        const uint32_t ph = (uint32_t)(k / kStages) & 1u;
+        if (k >= kStages && !mbar_wait(&empty[s], ph ^ 1u)) break;
+        const int64_t first = t * kT;
+        const int64_t m = (a.n - first < kT) ? a.n - first : kT;
+        const uint32_t cols = (uint32_t)(((m + W - 1) / W) * W);  // whole blocks
+        unsigned char *st = smem + s * kStageB;
+        mbar_arrive_expect_tx(&full[s], cols * (6 + 21 + 3 + 6) * 4);
+        bulk_g2s(st, a.state_in + first * 6, cols * 6 * 4, &full[s]);
+        bulk_g2s(st + kStateB, a.cov_in + first * 21, cols * 21 * 4, &full[s]);
+        bulk_g2s(st + kStateB + kCovB, a.hit + first * 3, cols * 3 * 4, &full[s]);
+        bulk_g2s(st + kStateB + kCovB + kHitB, a.hitcov + first * 6, cols * 6 * 4, &full[s]);
+      }
+    }
+    return;
+  }
+
+  // --------------------------------------------------------------- compute
+  const int il = warp * 32 + lane;          // track within the tile
+  const int blk = il / W, r = il % W;       // AoSoA block and slot within the tile
+  int k = 0;
+  for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x, ++k) {
+    const int s = k % kStages;
+    const uint32_t ph = (uint32_t)(k / kStages) & 1u;
+    const int64_t i = t * kT + il;
+    const bool live = i < a.n;
+    // plain per-track arrays: issue before waiting on the stage
+    const float qf = live ? (float)__ldg(a.charge + i) : 1.0f;
+    const float surf = __ldg(a.surf + ((a.surf_per_track && live) ? i : 0));
+    if (!mbar_wait(&full[s], ph)) break;
+
+    const float *sst = reinterpret_cast<const float *>(smem + s * kStageB);
+    const float *scv = sst + kT * 6;
+    const float *sht = scv + kT * 21;
+    const float *shc = sht + kT * 3;
+    float p[6], C[21];
+#pragma unroll
+    for (int c = 0; c < 6; ++c) p[c] = sst[blk * 6 * W + c * W + r];
+#pragma unroll
+    for (int e = 0; e < 21; ++e) C[e] = scv[blk * 21 * W + e * W + r];
+    const float hx = sht[blk * 3 * W + r];
+    const float hy = sht[blk * 3 * W + W + r];
+    float hz = 0.0f, hc[6];
+    if (KIND == kP2r) {
+      hz = sht[blk * 3 * W + 2 * W + r];
+#pragma unroll
+      for (int c = 0; c < 6; ++c) hc[c] = shc[blk * 6 * W + c * W + r];
+    } else {
+#pragma unroll
+      for (int c = 0; c < 3; ++c) hc[c] = shc[blk * 6 * W + c * W + r];
+      hc[3] = hc[4] = hc[5] = 0.0f;
+    }
+    __syncwarp();
+    if (lane == 0) mbar_arrive(&empty[s]);  // stage may be refilled
+    if (!live) continue;
+
+    unsigned st;
+    if (KIND == kP2z)
+      st = p2z_step<VARIANT>(p, C, qf, a.bz, surf, hx, hy, hc[0], hc[1], hc[2]);
+    else
+      st = p2r_step<VARIANT>(p, C, qf, a.bz, surf, hx, hy, hz, hc);
+    st |= finite_status(p, C);
+
+    const int64_t b6 = (i / W) * (6 * W) + (i % W);
+    const int64_t b21 = (i / W) * (21 * W) + (i % W);
+#pragma unroll
+    for (int c = 0; c < 6; ++c) __stcs(a.state_out + b6 + c * W, p[c]);
+#pragma unroll
+    for (int e = 0; e < 21; ++e) __stcs(a.cov_out + b21 + e * W, C[e]);
+    if (a.status) a.status[i] = (uint8_t)st;
+  }
+}
+
+template <int KIND, int VARIANT, int W>
+int launch_w(const StepArgs &a, cudaStream_t s, int grid, int dev) {
+  auto kern = step_staged_kernel<KIND, VARIANT, W>;
+  static bool configured[64] = {};  // per instantiation and device
+  if (dev < 0 || dev >= 64 || !configured[dev]) {
+    if (int rc = check_cuda(
+            cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes),
+            "cudaFuncSetAttribute"))
+      return rc;
+    if (dev >= 0 && dev < 64) configured[dev] = true;
+  }
+  kern<<<grid, kThreads, kSmemBytes, s>>>(a);
+  return check_cuda(cudaGetLastError(), "staged step launch");
+}
+
+template <int KIND, int VARIANT>
+int launch_v(const StepArgs &a, cudaStream_t s, int grid, int dev) {
+  switch (a.lw) {
+    case 4: return launch_w<KIND, VARIANT, 16>(a, s, grid, dev);
+    case 5: return launch_w<KIND, VARIANT, 32>(a, s, grid, dev);
+    case 6: return launch_w<KIND, VARIANT, 64>(a, s, grid, dev);
+    default: return launch_w<KIND, VARIANT, 128>(a, s, grid, dev);
+  }
+}
+
+std::mutex g_sm_mu;
+int g_sm_count[64] = {};
+
+int sm_count(int dev, int *out) {
+  std::lock_guard<std::mutex> lock(g_sm_mu);
+  if (dev >= 0 && dev < 64 && g_sm_count[dev] > 0) {
+    *out = g_sm_count[dev];
+    return KF_OK;
+  }
+  int v = 0;
+  if (int rc = check_cuda(cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev),
+                          "cudaDeviceGetAttribute"))
+    return rc;
+  if (dev >= 0 && dev < 64) g_sm_count[dev] = v;
+  *out = v;
+  return KF_OK;
+}
+
+}  // namespace staged
+
+// Persistent staged launch for AoSoA layouts: two CTAs per SM, each looping
+// over tiles blockIdx.x, blockIdx.x + gridDim.x, ...
+int launch_step_staged(int kind, int precision, const StepArgs &a, cudaStream_t s) {
+  using namespace staged;
+  if (a.n == 0) return KF_OK;
+  if (a.soa) return set_error(KF_ERR_UNSUPPORTED, "the staged kernel takes AoSoA layouts");
+  int dev = 0, sms = 0;
+  if (int rc = check_cuda(cudaGetDevice(&dev), "cudaGetDevice")) return rc;
+  if (int rc = sm_count(dev, &sms)) return rc;
+  const int64_t ntiles = (a.n + kT - 1) / kT;
+  const int grid = (int)((ntiles < 2 * (int64_t)sms) ? ntiles : 2 * (int64_t)sms);
+  if (kind == kP2z) {
+    switch (precision) {
+      case KF_FP32: return launch_v<kP2z, kFP32>(a, s, grid, dev);
+      case KF_FP64_UPDATE: return launch_v<kP2z, kFP64Update>(a, s, grid, dev);
+      default: return launch_v<kP2z, kJoseph>(a, s, grid, dev);
+    }
+  }
+  switch (precision) {
+    case KF_FP32: return launch_v<kP2r, kFP32>(a, s, grid, dev);
+    case KF_FP64_UPDATE: return launch_v<kP2r, kFP64Update>(a, s, grid, dev);
+    default: return launch_v<kP2r, kJoseph>(a, s, grid, dev);
+  }
+}
+
+}  // namespace kf
+
+extern "C" int kf_take_device_error(unsigned int *error_bits) {
+  kf::clear_error();
+  if (!error_bits) return kf::set_error(KF_ERR_ARG, "error_bits is NULL");
+  unsigned int v = 0, zero = 0;
+  if (int rc = kf::check_cuda(cudaMemcpyFromSymbol(&v, kf::g_device_error, sizeof(v)),
+                              "read device error word"))
+    return rc;
+  if (int rc = kf::check_cuda(cudaMemcpyToSymbol(kf::g_device_error, &zero, sizeof(zero)),
+                              "clear device error word"))
+    return rc;
+  *error_bits = v;
+  return KF_OK;
+}

@@ -42,6 +42,27 @@ class kf_params(ctypes.Structure):
     _fields_ = [("bz", ctypes.c_float), ("precision", ctypes.c_int32), ("flags", ctypes.c_uint32)]
 
 
+class kf_layer(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("pos", ctypes.c_float)]
+
+
+KF_MAX_LAYERS = 64
+
+
+class kf_server_config(ctypes.Structure):
+    _fields_ = [("bz", ctypes.c_float), ("precision", ctypes.c_int32), ("L", ctypes.c_int32),
+                ("layers", kf_layer * KF_MAX_LAYERS), ("arena", ctypes.c_void_p),
+                ("arena_bytes", ctypes.c_int64), ("max_events_in_flight", ctypes.c_int32),
+                ("device", ctypes.c_int32)]
+
+
+class kf_server_stats(ctypes.Structure):
+    _fields_ = [("events_done", ctypes.c_int64), ("tracks_done", ctypes.c_int64),
+                ("batches", ctypes.c_int64), ("max_batch_events", ctypes.c_int64),
+                ("p50_ms", ctypes.c_double), ("p99_ms", ctypes.c_double),
+                ("max_ms", ctypes.c_double), ("mean_ms", ctypes.c_double)]
+
+
 _lib = None
 _VP = ctypes.c_void_p
 
@@ -70,6 +91,33 @@ def load():
     lib.kf_propagate_update_host_noalloc.restype = ctypes.c_int
     lib.kf_host_workspace_bytes.argtypes = [kf_layout, ctypes.c_int64]
     lib.kf_host_workspace_bytes.restype = ctypes.c_int64
+    lib.kf_kalman_chain.argtypes = [ctypes.POINTER(kf_params), kf_layout, _VP, _VP, _VP, _VP,
+                                    _VP, ctypes.POINTER(kf_layer), ctypes.c_int32, _VP, _VP]
+    lib.kf_kalman_chain.restype = ctypes.c_int
+    lib.kf_propagate_update_compressed.argtypes = [ctypes.c_int32, ctypes.POINTER(kf_params),
+                                                   kf_layout] + [_VP] * 10 + [ctypes.c_int32,
+                                                                              _VP, _VP]
+    lib.kf_propagate_update_compressed.restype = ctypes.c_int
+    srv = ctypes.c_void_p
+    lib.kf_server_event_bytes.argtypes = [ctypes.c_int64, ctypes.c_int32]
+    lib.kf_server_event_bytes.restype = ctypes.c_int64
+    lib.kf_server_create.argtypes = [ctypes.POINTER(kf_server_config), ctypes.POINTER(srv)]
+    lib.kf_server_submit.argtypes = [srv, ctypes.c_int64] + [_VP] * 8 + [
+        ctypes.POINTER(ctypes.c_uint64)]
+    lib.kf_server_poll.argtypes = [srv, ctypes.c_uint64, ctypes.POINTER(ctypes.c_int32)]
+    lib.kf_server_wait.argtypes = [srv, ctypes.c_uint64, ctypes.c_double]
+    lib.kf_server_pause.argtypes = [srv, ctypes.c_int32]
+    lib.kf_server_get_stats.argtypes = [srv, ctypes.POINTER(kf_server_stats)]
+    lib.kf_server_reset_stats.argtypes = [srv]
+    lib.kf_server_destroy.argtypes = [srv]
+    for name in ("kf_server_create", "kf_server_submit", "kf_server_poll", "kf_server_wait",
+                 "kf_server_pause", "kf_server_get_stats", "kf_server_reset_stats",
+                 "kf_server_destroy"):
+        getattr(lib, name).restype = ctypes.c_int
+    lib.kf_set_step_kernel.argtypes = [ctypes.c_int32]
+    lib.kf_set_step_kernel.restype = ctypes.c_int
+    lib.kf_take_device_error.argtypes = [ctypes.POINTER(ctypes.c_uint)]
+    lib.kf_take_device_error.restype = ctypes.c_int
     lib.kf_version.restype = ctypes.c_int
     lib.kf_last_error_string.restype = ctypes.c_char_p
     _lib = lib
@@ -218,6 +266,66 @@ def kf_propagate_update_host_noalloc(kind, params, layout, state_in, cov_in, sta
 
 def kf_host_workspace_bytes(layout, chunk_tracks: int = 0) -> int:
     return int(load().kf_host_workspace_bytes(layout, int(chunk_tracks)))
+
+
+def make_layers(kinds, pos):
+    arr = (kf_layer * len(kinds))()
+    for l, (k, z) in enumerate(zip(kinds, pos)):
+        arr[l].kind = int(k)
+        arr[l].pos = float(z)
+    return arr
+
+
+def kf_kalman_chain(params, layout, state, cov, charge, hits, hit_covs, layers, status=None,
+                    stream=None):
+    """C-ABI kf_kalman_chain (in place on state/cov); `layers` from make_layers()."""
+    lib = load()
+    f32, i8, u8 = torch.float32, torch.int8, torch.uint8
+    rc = lib.kf_kalman_chain(ctypes.byref(params), layout, _ptr(state, "state", f32),
+                             _ptr(cov, "cov", f32), _ptr(charge, "charge", i8),
+                             _ptr(hits, "hits", f32), _ptr(hit_covs, "hit_covs", f32),
+                             layers, len(layers), _ptr(status, "status", u8), _stream(stream))
+    _check(rc)
+
+
+def kf_propagate_update_compressed(kind, params, layout, state_in, sigma_in, rho_in, state_out,
+                                   sigma_out, rho_out, charge, hit, hit_cov, surf,
+                                   surf_per_track=0, status=None, stream=None):
+    """C-ABI kf_propagate_update_compressed; rho tensors hold float16 (or int16 bits)."""
+    lib = load()
+    f32, i8, u8 = torch.float32, torch.int8, torch.uint8
+    rc = lib.kf_propagate_update_compressed(
+        int(kind), ctypes.byref(params), layout, _ptr(state_in, "state_in", f32),
+        _ptr(sigma_in, "sigma_in", f32), _ptr(rho_in, "rho_in", torch.float16),
+        _ptr(state_out, "state_out", f32), _ptr(sigma_out, "sigma_out", f32),
+        _ptr(rho_out, "rho_out", torch.float16), _ptr(charge, "charge", i8),
+        _ptr(hit, "hit", f32), _ptr(hit_cov, "hit_cov", f32), _ptr(surf, "surf", f32),
+        int(surf_per_track), _ptr(status, "status", u8), _stream(stream))
+    _check(rc)
+
+
+def to_device_half(a: np.ndarray, layout: kf_layout, device) -> torch.Tensor:
+    """[C, n] float16 SoA -> a flat device tensor in `layout`."""
+    a = np.ascontiguousarray(a, dtype=np.float16)
+    if layout.kind == KF_AOSOA:
+        a = W.to_aosoa(a, layout.width)
+    return torch.from_numpy(a.reshape(-1).copy()).to(device)
+
+
+KF_STEP_AUTO, KF_STEP_DIRECT, KF_STEP_STAGED = 0, 1, 2
+KF_DEVERR_TIMEOUT = 1
+
+
+def kf_set_step_kernel(mode: int) -> None:
+    """C-ABI kf_set_step_kernel: KF_STEP_AUTO / KF_STEP_DIRECT / KF_STEP_STAGED."""
+    _check(load().kf_set_step_kernel(int(mode)))
+
+
+def kf_take_device_error() -> int:
+    """C-ABI kf_take_device_error: read and clear the device error word."""
+    v = ctypes.c_uint(0)
+    _check(load().kf_take_device_error(ctypes.byref(v)))
+    return int(v.value)
 
 
 def kf_version() -> int:
@@ -372,3 +480,129 @@ def host_upload(w: W.Workload, layout_kind: int = KF_SOA, width: int = 32, devic
                      state_out=st_out, cov_out=cv_out, charge=q, hit=host(w.hit),
                      hit_cov=host(w.hitcov), surf=surf, status=status, workspace=ws, bz=w.bz,
                      chunk_tracks=chunk_tracks)
+
+
+@dataclasses.dataclass
+class DeviceChain:
+    """A chain workload resident on the GPU (plumbing only)."""
+    n: int
+    layout: kf_layout
+    layers: object
+    state0: torch.Tensor    # start state, kept to reset between runs
+    cov0: torch.Tensor
+    state: torch.Tensor     # worked on in place
+    cov: torch.Tensor
+    charge: torch.Tensor
+    hits: torch.Tensor      # L consecutive hit arrays
+    hit_covs: torch.Tensor
+    status: torch.Tensor
+    bz: float
+    f3: int
+    f6: int
+
+    def reset(self):
+        self.state.copy_(self.state0)
+        self.cov.copy_(self.cov0)
+
+    def run(self, precision: int = KF_FP32, stream=None):
+        kf_kalman_chain(make_params(self.bz, precision), self.layout, self.state, self.cov,
+                        self.charge, self.hits, self.hit_covs, self.layers, self.status, stream)
+
+    def run_plain(self, precision: int = KF_FP32, stream=None):
+        """The same chain as L single-step launches, in place."""
+        p = make_params(self.bz, precision)
+        for l in range(len(self.layers)):
+            fn = kf_p2z_propagate_update if self.layers[l].kind == 0 else kf_p2r_propagate_update
+            surf = self._surf[l]
+            fn(p, self.layout, self.state, self.cov, self.state, self.cov, self.charge,
+               self.hits[l * self.f3:(l + 1) * self.f3], self.hit_covs[l * self.f6:(l + 1) * self.f6],
+               surf, 0, self.status, stream)
+
+    def download(self):
+        return (from_device(self.state, 6, self.n, self.layout),
+                from_device(self.cov, 21, self.n, self.layout), self.status.cpu().numpy())
+
+
+def chain_upload(cw, layout_kind: int = KF_AOSOA, width: int = 32, device="cuda") -> DeviceChain:
+    lay = make_layout(layout_kind, width, cw.n)
+    st = to_device(cw.state, lay, device)
+    cv = to_device(cw.cov, lay, device)
+    hits = torch.cat([to_device(cw.hit[l], lay, device) for l in range(cw.L)])
+    hcs = torch.cat([to_device(cw.hitcov[l], lay, device) for l in range(cw.L)])
+    f3 = hits.numel() // cw.L
+    f6 = hcs.numel() // cw.L
+    dc = DeviceChain(n=cw.n, layout=lay, layers=make_layers(cw.kinds, cw.pos), state0=st,
+                     cov0=cv, state=st.clone(), cov=cv.clone(),
+                     charge=torch.from_numpy(np.ascontiguousarray(cw.charge)).to(device),
+                     hits=hits, hit_covs=hcs,
+                     status=torch.zeros(cw.n, dtype=torch.uint8, device=device), bz=cw.bz,
+                     f3=f3, f6=f6)
+    dc._surf = [torch.tensor([float(z)], dtype=torch.float32, device=device) for z in cw.pos]
+    return dc
+
+
+# ------------------------------------------------------------ serving loop
+
+class Server:
+    """Thin wrapper over kf_server_* (C ABI): one object per server."""
+
+    def __init__(self, bz, kinds, pos, arena: torch.Tensor, max_events_in_flight=64,
+                 precision=KF_FP32):
+        lib = load()
+        if not arena.is_cuda:
+            raise ValueError("arena must be a CUDA tensor")
+        cfg = kf_server_config()
+        cfg.bz = float(bz)
+        cfg.precision = int(precision)
+        cfg.L = len(kinds)
+        for l, (k, z) in enumerate(zip(kinds, pos)):
+            cfg.layers[l].kind = int(k)
+            cfg.layers[l].pos = float(z)
+        cfg.arena = arena.data_ptr()
+        cfg.arena_bytes = arena.numel() * arena.element_size()
+        cfg.max_events_in_flight = int(max_events_in_flight)
+        cfg.device = arena.device.index or 0
+        self._arena = arena
+        self._h = ctypes.c_void_p()
+        _check(lib.kf_server_create(ctypes.byref(cfg), ctypes.byref(self._h)))
+        self.L = cfg.L
+        self._keep = {}
+
+    def submit(self, state, cov, charge, hits, hit_covs, state_out, cov_out, status_out=None):
+        """Host tensors (SoA per event).  Returns a ticket."""
+        t = ctypes.c_uint64(0)
+        n = state.shape[-1]
+        args = [state, cov, charge, hits, hit_covs, state_out, cov_out, status_out]
+        ptrs = [None if a is None else _host_ptr(a, "event array", a.dtype) for a in args]
+        _check(load().kf_server_submit(self._h, int(n), *ptrs, ctypes.byref(t)))
+        self._keep[t.value] = args
+        return t.value
+
+    def poll(self, ticket) -> bool:
+        d = ctypes.c_int32(0)
+        _check(load().kf_server_poll(self._h, ctypes.c_uint64(ticket), ctypes.byref(d)))
+        return bool(d.value)
+
+    def wait(self, ticket, timeout_s=60.0):
+        _check(load().kf_server_wait(self._h, ctypes.c_uint64(ticket), float(timeout_s)))
+        self._keep.pop(ticket, None)
+
+    def pause(self, paused=True):
+        _check(load().kf_server_pause(self._h, int(bool(paused))))
+
+    def stats(self) -> dict:
+        st = kf_server_stats()
+        _check(load().kf_server_get_stats(self._h, ctypes.byref(st)))
+        return {f: getattr(st, f) for f, _ in st._fields_}
+
+    def reset_stats(self):
+        _check(load().kf_server_reset_stats(self._h))
+
+    def close(self):
+        if self._h:
+            _check(load().kf_server_destroy(self._h))
+            self._h = ctypes.c_void_p()
+
+
+def kf_server_event_bytes(n: int, L: int) -> int:
+    return int(load().kf_server_event_bytes(int(n), int(L)))

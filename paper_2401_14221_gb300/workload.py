@@ -452,3 +452,39 @@ def make_chain(events: int = 256, seed: int = 1, sizes: Optional[np.ndarray] = N
                          truth_index=idx,
                          description=(f"chain {len(sizes)} events, {n} tracks, {L} layers, "
                                       f"{m} simulated true tracks"))
+
+
+# --------------------------------------------- compressed covariance format
+
+# Off-diagonal entries (i > j) in packed lower-triangular order:
+# 10, 20, 21, 30, 31, 32, 40, ..., 54.
+OFFDIAG = [(i, j) for i in range(6) for j in range(i)]
+
+
+def compress_cov(cov: np.ndarray):
+    """[21, n] packed covariance -> (sigma float32 [6, n], rho float16 [15, n]):
+    sigma_i = sqrt(C_ii), rho_ij = C_ij / (sigma_i sigma_j) clamped to [-1, 1]
+    (0 where a sigma is 0), rounded to nearest in each format."""
+    cov = np.asarray(cov, dtype=np.float64)
+    diag = np.stack([cov[tri_index(i, i)] for i in range(6)])
+    sig = np.sqrt(np.maximum(diag, 0.0)).astype(np.float32)
+    s64 = sig.astype(np.float64)
+    rho = np.empty((15, cov.shape[1]), dtype=np.float64)
+    for k, (i, j) in enumerate(OFFDIAG):
+        den = s64[i] * s64[j]
+        with np.errstate(divide="ignore", invalid="ignore"):
+            r = np.where(den > 0, cov[tri_index(i, j)] / np.where(den > 0, den, 1.0), 0.0)
+        rho[k] = np.clip(r, -1.0, 1.0)
+    return sig, rho.astype(np.float16)
+
+
+def decompress_cov(sig: np.ndarray, rho: np.ndarray) -> np.ndarray:
+    """(sigma [6, n], rho [15, n]) -> [21, n] packed covariance in float64."""
+    s = np.asarray(sig, dtype=np.float64)
+    r = np.asarray(rho, dtype=np.float64)
+    out = np.empty((21, s.shape[1]))
+    for i in range(6):
+        out[tri_index(i, i)] = s[i] * s[i]
+    for k, (i, j) in enumerate(OFFDIAG):
+        out[tri_index(i, j)] = r[k] * s[i] * s[j]
+    return out

@@ -1,0 +1,111 @@
+"""The fused multi-layer chain kernel through the C ABI: against the single
+step, against L separate single-step launches, and against the FP64 oracle's
+chain on the 256-event workload (sampled)."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from oracle import compare
+from paper_2401_14221_gb300 import build as kbuild
+from paper_2401_14221_gb300 import kf
+from paper_2401_14221_gb300 import workload as W
+
+pytestmark = pytest.mark.gpu
+
+VARIANT_FORM = {kf.KF_FP32: oracle.FORM_STANDARD, kf.KF_FP64_UPDATE: oracle.FORM_STANDARD,
+                kf.KF_JOSEPH: oracle.FORM_JOSEPH}
+
+
+@pytest.fixture(scope="module")
+def dev():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    kbuild.build()
+    torch.cuda.set_device(0)
+    yield torch.device("cuda:0")
+    assert kf.kf_take_device_error() == 0
+
+
+@pytest.fixture(scope="module")
+def chain_full():
+    return W.make_chain(events=256, seed=1)
+
+
+def oracle_chain(cw, idx, form=oracle.FORM_STANDARD):
+    hit = np.ascontiguousarray(cw.hit[:, :, idx].transpose(0, 2, 1), dtype=np.float64)
+    hc = np.ascontiguousarray(cw.hitcov[:, :, idx].transpose(0, 2, 1), dtype=np.float64)
+    return oracle.chain_batch(cw.kinds, cw.pos, cw.state.T[idx], cw.cov.T[idx], cw.charge[idx],
+                              hit, hc, cw.bz, form, threads=8)
+
+
+def ends_on_cylinder(cw, o_st):
+    """Tracks whose last reached layer is a cylinder (their covariance is
+    compared in that surface's frame)."""
+    r = np.hypot(o_st[:, 0], o_st[:, 1])
+    on_plane = np.isin(o_st[:, 2], cw.pos[cw.kinds == W.P2Z].astype(np.float64))
+    on_cyl = np.zeros(len(o_st), dtype=bool)
+    for R in cw.pos[cw.kinds == W.P2R].astype(np.float64):
+        on_cyl |= np.abs(r - R) <= 1e-5 * R
+    return on_cyl & ~on_plane
+
+
+@pytest.mark.parametrize("kind", [W.P2Z, W.P2R])
+@pytest.mark.parametrize("layout", [(kf.KF_SOA, 0), (kf.KF_AOSOA, 32)])
+def test_chain_of_one_layer_equals_single_step_bitwise(dev, kind, layout):
+    w = W.make_p2z(20011, seed=41) if kind == W.P2Z else W.make_p2r(1, 20011, seed=41)
+    b = kf.upload(w, layout[0], layout[1], dev)
+    b.run()
+    ref = b.download()
+    cw = W.ChainWorkload(n=w.n, bz=w.bz, kinds=np.array([kind], dtype=np.int32),
+                         pos=np.array([w.surf], dtype=np.float32), event_sizes=np.array([w.n]),
+                         state=w.state, cov=w.cov, charge=w.charge, hit=w.hit[None],
+                         hitcov=w.hitcov[None], truth_pool_layers=np.zeros((1, 6, 1)),
+                         truth_index=np.zeros(w.n, dtype=np.int64))
+    dc = kf.chain_upload(cw, layout[0], layout[1], dev)
+    dc.run()
+    got = dc.download()
+    for a, c in zip(ref, got):
+        assert np.array_equal(a, c)
+
+
+@pytest.mark.parametrize("precision", [kf.KF_FP32, kf.KF_JOSEPH])
+def test_chain_equals_per_layer_launches_bitwise(dev, precision):
+    cw = W.make_chain(events=6, seed=42)
+    dc = kf.chain_upload(cw, kf.KF_AOSOA, 32, dev)
+    dc.run(precision)
+    fused = dc.download()
+    dc.reset()
+    dc.run_plain(precision)
+    plain = dc.download()
+    assert np.array_equal(fused[0], plain[0]) and np.array_equal(fused[1], plain[1])
+
+
+@pytest.mark.parametrize("precision", [kf.KF_FP32, kf.KF_FP64_UPDATE, kf.KF_JOSEPH])
+def test_chain_matches_oracle_on_256_events(dev, chain_full, precision):
+    cw = chain_full
+    dc = kf.chain_upload(cw, kf.KF_AOSOA, 32, dev)
+    dc.run(precision)
+    st, cv, stat = dc.download()
+    n = cw.n
+    idx = np.unique(np.concatenate([np.arange(200), np.linspace(0, n - 1, 3000).astype(np.int64),
+                                    np.arange(n - 200, n)]))
+    o_st, o_cv, o_stat = oracle_chain(cw, idx, VARIANT_FORM[precision])
+    rep = compare.compare(st.T[idx], cv.T[idx], stat[idx], o_st, o_cv, o_stat,
+                          on_cylinder=ends_on_cylinder(cw, o_st))
+    assert rep["ok"], rep
+
+
+def test_empty_chain_and_bad_layers(dev):
+    cw = W.make_chain(events=1, seed=43, sizes=np.array([100]))
+    dc = kf.chain_upload(cw, kf.KF_SOA, 0, dev)
+    before = dc.state.clone()
+    kf.kf_kalman_chain(kf.make_params(cw.bz), dc.layout, dc.state, dc.cov, dc.charge, dc.hits,
+                       dc.hit_covs, kf.make_layers([], []))
+    torch.cuda.synchronize()
+    assert torch.equal(before, dc.state)
+    bad = kf.make_layers([5], [30.0])
+    with pytest.raises(kf.KfError) as e:
+        kf.kf_kalman_chain(kf.make_params(cw.bz), dc.layout, dc.state, dc.cov, dc.charge,
+                           dc.hits, dc.hit_covs, bad)
+    assert e.value.code == kf.KF_ERR_ARG

@@ -1,0 +1,185 @@
+"""The continuous-batching server (kf_server_*) through the C ABI.
+
+Each event's result must be the same alone and in the mix: events run
+alone through kf_kalman_chain give the reference, then all events go
+through the server concurrently (batched with whatever else is in flight);
+the results must match bit for bit (one thread per track, same arithmetic).
+Failure paths are exercised on the host: a paused server makes a bounded
+wait time out, and an event larger than the arena is refused."""
+import threading
+import time
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from oracle import compare
+from paper_2401_14221_gb300 import build as kbuild
+from paper_2401_14221_gb300 import kf
+from paper_2401_14221_gb300 import workload as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def dev():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    kbuild.build()
+    torch.cuda.set_device(0)
+    return torch.device("cuda:0")
+
+
+@pytest.fixture(scope="module")
+def events():
+    rng = np.random.default_rng(5)
+    sizes = W.lognormal_event_sizes(rng, 40, median=800.0, lo=50, hi=6000)
+    return W.make_chain(events=len(sizes), seed=51, sizes=sizes, pool=20000)
+
+
+def event_arrays(cw, e):
+    lo = int(cw.event_sizes[:e].sum())
+    hi = lo + int(cw.event_sizes[e])
+    pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
+    ins = (pin(cw.state[:, lo:hi]), pin(cw.cov[:, lo:hi]), pin(cw.charge[lo:hi]),
+           pin(cw.hit[:, :, lo:hi]), pin(cw.hitcov[:, :, lo:hi]))
+    n = hi - lo
+    outs = (torch.empty((6, n), dtype=torch.float32).pin_memory(),
+            torch.empty((21, n), dtype=torch.float32).pin_memory(),
+            torch.empty(n, dtype=torch.uint8).pin_memory())
+    return lo, hi, ins, outs
+
+
+def alone(cw, e, dev):
+    lo, hi = int(cw.event_sizes[:e].sum()), int(cw.event_sizes[:e + 1].sum())
+    sub = W.ChainWorkload(n=hi - lo, bz=cw.bz, kinds=cw.kinds, pos=cw.pos,
+                          event_sizes=np.array([hi - lo]), state=cw.state[:, lo:hi],
+                          cov=cw.cov[:, lo:hi], charge=cw.charge[lo:hi], hit=cw.hit[:, :, lo:hi],
+                          hitcov=cw.hitcov[:, :, lo:hi], truth_pool_layers=cw.truth_pool_layers,
+                          truth_index=cw.truth_index[lo:hi])
+    dc = kf.chain_upload(sub, kf.KF_SOA, 0, dev)
+    dc.run()
+    return dc.download()
+
+
+def make_server(cw, dev, arena_bytes, slots=64):
+    arena = torch.empty(arena_bytes, dtype=torch.uint8, device=dev)
+    return kf.Server(cw.bz, cw.kinds, cw.pos, arena, max_events_in_flight=slots)
+
+
+def test_results_alone_equal_results_in_the_mix(dev, events):
+    cw = events
+    refs = [alone(cw, e, dev) for e in range(len(cw.event_sizes))]
+    srv = make_server(cw, dev, 512 << 20)
+    try:
+        arrays = [event_arrays(cw, e) for e in range(len(cw.event_sizes))]
+        tickets = [None] * len(arrays)
+
+        def submit(idx, gap):
+            for e in idx:
+                _, _, ins, outs = arrays[e]
+                tickets[e] = srv.submit(*ins, *outs)
+                time.sleep(gap * (e % 3))
+        # first half: two threads submit while the server is paused, so the
+        # events share batches; second half: submitted while batches run
+        half = len(arrays) // 2
+        srv.pause(True)
+        th = [threading.Thread(target=submit, args=(range(k, half, 2), 0.0)) for k in (0, 1)]
+        for t in th:
+            t.start()
+        for t in th:
+            t.join()
+        srv.pause(False)
+        th = [threading.Thread(target=submit, args=(range(half + k, len(arrays), 2), 2e-4))
+              for k in (0, 1)]
+        for t in th:
+            t.start()
+        for t in th:
+            t.join()
+        for e, t in enumerate(tickets):
+            srv.wait(t, 60.0)
+        st = srv.stats()
+        assert st["events_done"] == len(arrays)
+        assert st["max_batch_events"] > 1  # requests were batched together
+        for e, (_, _, _, outs) in enumerate(arrays):
+            ref = refs[e]
+            assert np.array_equal(outs[0].numpy(), ref[0])
+            assert np.array_equal(outs[1].numpy(), ref[1])
+            assert np.array_equal(outs[2].numpy(), ref[2])
+    finally:
+        srv.close()
+
+
+def test_server_results_match_the_oracle(dev, events):
+    cw = events
+    srv = make_server(cw, dev, 256 << 20)
+    try:
+        for e in range(0, len(cw.event_sizes), 9):
+            lo, hi, ins, outs = event_arrays(cw, e)
+            srv.wait(srv.submit(*ins, *outs))
+            hit = np.ascontiguousarray(cw.hit[:, :, lo:hi].transpose(0, 2, 1), dtype=np.float64)
+            hc = np.ascontiguousarray(cw.hitcov[:, :, lo:hi].transpose(0, 2, 1), dtype=np.float64)
+            o_st, o_cv, o_stat = oracle.chain_batch(cw.kinds, cw.pos, cw.state.T[lo:hi],
+                                                    cw.cov.T[lo:hi], cw.charge[lo:hi], hit, hc,
+                                                    cw.bz)
+            r = np.hypot(o_st[:, 0], o_st[:, 1])
+            on_plane = np.isin(o_st[:, 2], cw.pos[cw.kinds == W.P2Z].astype(np.float64))
+            on_cyl = np.zeros(hi - lo, dtype=bool)
+            for R in cw.pos[cw.kinds == W.P2R].astype(np.float64):
+                on_cyl |= np.abs(r - R) <= 1e-5 * R
+            rep = compare.compare(outs[0].numpy().T, outs[1].numpy().T, outs[2].numpy(), o_st,
+                                  o_cv, o_stat, on_cylinder=on_cyl & ~on_plane)
+            assert rep["ok"], rep
+    finally:
+        srv.close()
+
+
+def test_admission_waits_for_arena_space(dev, events):
+    # an arena that holds about two of the largest events: the rest wait
+    cw = events
+    sizes = cw.event_sizes[:12]
+    arena_bytes = 2 * kf.kf_server_event_bytes(int(sizes.max()), cw.L) + 4096
+    fits = arena_bytes // kf.kf_server_event_bytes(int(sizes.min()), cw.L)
+    srv = make_server(cw, dev, arena_bytes)
+    try:
+        arrays = [event_arrays(cw, e) for e in range(12)]
+        tickets = [srv.submit(*a[2], *a[3]) for a in arrays]
+        for t in tickets:
+            srv.wait(t, 60.0)
+        st = srv.stats()
+        assert st["events_done"] == 12 and st["max_batch_events"] <= min(fits, 11)
+        for e, (_, _, _, outs) in enumerate(arrays):
+            ref = alone(cw, e, dev)
+            assert np.array_equal(outs[0].numpy(), ref[0])
+    finally:
+        srv.close()
+
+
+def test_paused_server_wait_times_out_then_completes(dev, events):
+    cw = events
+    srv = make_server(cw, dev, 64 << 20)
+    try:
+        srv.pause(True)
+        _, _, ins, outs = event_arrays(cw, 0)
+        t = srv.submit(*ins, *outs)
+        with pytest.raises(kf.KfError) as e:
+            srv.wait(t, 0.05)
+        assert e.value.code == kf.KF_ERR_TIMEOUT
+        assert not srv.poll(t)
+        srv.pause(False)
+        srv.wait(t, 60.0)
+    finally:
+        srv.close()
+
+
+def test_event_larger_than_arena_is_refused(dev, events):
+    cw = events
+    srv = make_server(cw, dev, 1 << 20)
+    try:
+        _, _, ins, outs = event_arrays(cw, int(np.argmax(cw.event_sizes)))
+        with pytest.raises(kf.KfError) as e:
+            srv.submit(*ins, *outs)
+        assert e.value.code == kf.KF_ERR_ARG
+    finally:
+        srv.close()

@@ -496,3 +496,42 @@ def test_batch_equals_single_track_calls():
         po, co, c2, s = oracle.step(oracle.P2Z, w.state[:, i], w.cov[:, i], int(w.charge[i]),
                                     w.hit[:, i], w.hitcov[:, i], w.bz, w.surf)
         assert np.all(po == st[i]) and np.all(co == cv[i]) and s == stat[i]
+
+
+# ------------------------------------------------------------ the chain
+
+def test_chain_statistics_after_fifteen_layers():
+    # The chain filters each track through 15 alternating cylinders and
+    # planes; with a correctly specified filter the final state at the last
+    # surface (r = 110 cm) has N(0, 1) pulls against the simulated truth.
+    cw = W.make_chain(events=8, seed=31, sizes=np.full(8, 5000), pool=40000)
+    hit = np.ascontiguousarray(cw.hit.transpose(0, 2, 1), dtype=np.float64)
+    hc = np.ascontiguousarray(cw.hitcov.transpose(0, 2, 1), dtype=np.float64)
+    st, cv, stat = oracle.chain_batch(cw.kinds, cw.pos, cw.state.T, cw.cov.T, cw.charge, hit, hc,
+                                      cw.bz, threads=4)
+    truth = cw.truth_layer(cw.L - 1).T
+    ok = (stat == 0) & np.isfinite(truth[:, 0])
+    assert ok.mean() > 0.7
+    s, t = st[ok], truth[ok]
+    a = np.arctan2(s[:, 1], s[:, 0])
+    u = np.stack([-np.sin(a), np.cos(a)], axis=1)
+    dt = np.einsum("ni,ni->n", u, s[:, :2] - t[:, :2])
+    Cxx, Cxy, Cyy = (cv[ok, W.tri_index(i, j)] for i, j in ((0, 0), (1, 0), (1, 1)))
+    var_t = u[:, 0] ** 2 * Cxx + 2 * u[:, 0] * u[:, 1] * Cxy + u[:, 1] ** 2 * Cyy
+    pulls = [dt / np.sqrt(var_t)]
+    for c in (2, 3, 4, 5):
+        d = s[:, c] - t[:, c]
+        if c == 4:
+            d = (d + math.pi) % (2 * math.pi) - math.pi
+        pulls.append(d / np.sqrt(cv[ok, W.tri_index(c, c)]))
+    for pl in pulls:
+        assert abs(pl.mean()) < 0.03 and abs(pl.std() - 1.0) < 0.03, (pl.mean(), pl.std())
+
+
+def test_chain_of_one_layer_is_the_single_step():
+    w = W.make_p2r(1, 300, seed=33)
+    st1, cv1, s1, _ = oracle.step_batch(oracle.P2R, w.state.T, w.cov.T, w.charge, w.hit.T,
+                                        w.hitcov.T, w.surf, w.bz)
+    st2, cv2, s2 = oracle.chain_batch([oracle.P2R], [w.surf], w.state.T, w.cov.T, w.charge,
+                                      w.hit.T[None], w.hitcov.T[None], w.bz)
+    assert np.array_equal(st1, st2) and np.array_equal(cv1, cv2) and np.array_equal(s1, s2)
