@@ -59,6 +59,12 @@ def parse():
     ap.add_argument("--no-chain", action="store_true",
                     help="skip the fused-chain vs per-layer-launch comparison")
     ap.add_argument("--chain-steps", type=int, default=10)
+    ap.add_argument("--no-variants", action="store_true")
+    ap.add_argument("--no-serving", action="store_true",
+                    help="skip the serving-loop measurement")
+    ap.add_argument("--serve-events", type=int, default=2048)
+    ap.add_argument("--serve-rates", type=float, nargs="+", default=[3000.0, 10000.0],
+                    help="Poisson arrival rates of the serving measurement, events/s")
     ap.add_argument("--profile-only", action="store_true",
                     help="run a few launches of one layout and exit (for ncu captures)")
     ap.add_argument("--kind", choices=["p2r", "p2z"], default="p2r",
@@ -225,6 +231,41 @@ def cpu_baseline(w):
                       f"{time.process_time() - c0:.1f} s CPU time"}
 
 
+def compressed_bench(kf, W, w, dev, kind, width):
+    """The step on the compressed covariance store (FP32 sigmas + FP16
+    correlations): 193 algorithmic bytes per p2r track instead of 253."""
+    import torch
+
+    lay = kf.make_layout(kind, width, w.n)
+    sig, rho = W.compress_cov(w.cov)
+    bufs = []
+    for _ in range(4):
+        st_in = kf.to_device(w.state, lay, dev)
+        sg_in = kf.to_device(sig, lay, dev)
+        rh_in = kf.to_device_half(rho, lay, dev)
+        bufs.append((st_in, sg_in, rh_in, torch.empty_like(st_in), torch.empty_like(sg_in),
+                     torch.empty_like(rh_in), torch.from_numpy(w.charge).to(dev),
+                     kf.to_device(w.hit, lay, dev), kf.to_device(w.hitcov, lay, dev),
+                     torch.tensor([w.surf], dtype=torch.float32, device=dev),
+                     torch.empty(w.n, dtype=torch.uint8, device=dev)))
+    p = kf.make_params(w.bz)
+
+    def run(b):
+        kf.kf_propagate_update_compressed(kf.KF_P2R, p, lay, b[0], b[1], b[2], b[3], b[4], b[5],
+                                          b[6], b[7], b[8], b[9], 0, b[10])
+    run(bufs[0])
+    torch.cuda.synchronize()
+    a, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    for i in range(100):
+        run(bufs[i % 4])
+    e.record()
+    torch.cuda.synchronize()
+    ms = a.elapsed_time(e) / 100
+    return {"ms": ms, "tracks_per_s": w.n / (ms * 1e-3), "bytes_per_track": 193,
+            "GBps": 193 * w.n / (ms * 1e-3) / 1e9, "kernel": "direct (one thread per track)"}
+
+
 def chain_bench(args, kf, W, dev, rank):
     """Fused 15-layer chain vs the same chain as 15 single-step launches, on
     the 256-event workload (lognormal event sizes).  Both run in place, so the
@@ -286,6 +327,124 @@ def chain_bench(args, kf, W, dev, rank):
             "bytes_per_track": {"fused": fused_b, "plain": plain_b},
             "plain_launch": "CUDA graph" if plain_graph is not None else "eager",
             "timing": f"median of {reps} runs, CUDA events, state reset outside the timed pair"}
+
+
+def serving_bench(args, kf, W, dev, rank):
+    """Poisson event stream through the continuous-batching server vs a
+    per-event synchronous baseline (copy in, chain, copy out, synchronise),
+    both fed the same arrival times.  Events come from the 256-event chain
+    workload (lognormal sizes), cycled; latency = arrival to results in host
+    memory."""
+    import threading
+
+    import numpy as np
+    import torch
+
+    from paper_2401_14221_gb300 import shard
+
+    cw = W.make_chain(events=256, seed=shard.rank_seed(11, rank))
+    bounds = np.concatenate([[0], np.cumsum(cw.event_sizes)])
+    E = len(cw.event_sizes)
+    pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
+    ev_in, ev_out = [], []
+    for e in range(E):
+        lo, hi = int(bounds[e]), int(bounds[e + 1])
+        ev_in.append((pin(cw.state[:, lo:hi]), pin(cw.cov[:, lo:hi]), pin(cw.charge[lo:hi]),
+                      pin(cw.hit[:, :, lo:hi]), pin(cw.hitcov[:, :, lo:hi])))
+        n = hi - lo
+        ev_out.append((torch.empty((6, n), dtype=torch.float32).pin_memory(),
+                       torch.empty((21, n), dtype=torch.float32).pin_memory(),
+                       torch.empty(n, dtype=torch.uint8).pin_memory()))
+    total = args.serve_events
+    order = np.arange(total) % E
+    tracks = int(sum(cw.event_sizes[order]))
+    arena = torch.empty(4 << 30, dtype=torch.uint8, device=dev)
+    srv = kf.Server(cw.bz, cw.kinds, cw.pos, arena, max_events_in_flight=256)
+    # warm-up: load the batched kernel's module and touch the arena
+    for t in [srv.submit(*ev_in[e], *ev_out[e]) for e in range(16)]:
+        srv.wait(t, 120.0)
+
+    def serve(rate, seed):
+        arrivals = np.cumsum(np.random.default_rng(seed).exponential(1.0 / rate, total))
+        srv.reset_stats()
+        tickets = [None] * total
+        t0 = time.perf_counter()
+
+        def produce():
+            for k in range(total):
+                dt = t0 + arrivals[k] - time.perf_counter()
+                if dt > 0:
+                    time.sleep(dt)
+                e = order[k]
+                tickets[k] = srv.submit(*ev_in[e], *ev_out[e])
+
+        th = threading.Thread(target=produce)
+        th.start()
+        th.join()
+        for t in tickets:
+            srv.wait(t, 120.0)
+        t_end = time.perf_counter()
+        st = srv.stats()
+        return arrivals, {"rate_events_per_s": rate, "tracks_per_s": tracks / (t_end - t0),
+                          "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"], "max_ms": st["max_ms"],
+                          "batches": st["batches"], "max_batch_events": st["max_batch_events"]}
+
+    runs = [serve(rate, 12 + rank + k) for k, rate in enumerate(args.serve_rates)]
+    srv.close()
+    del arena
+
+    # --- per-event synchronous baseline on the same arrival times
+    nmax = int(cw.event_sizes.max())
+    L = cw.L
+    d_state = torch.empty(6 * nmax, dtype=torch.float32, device=dev)
+    d_cov = torch.empty(21 * nmax, dtype=torch.float32, device=dev)
+    d_q = torch.empty(nmax, dtype=torch.int8, device=dev)
+    d_hits = torch.empty(3 * nmax * L, dtype=torch.float32, device=dev)
+    d_hc = torch.empty(6 * nmax * L, dtype=torch.float32, device=dev)
+    d_status = torch.empty(nmax, dtype=torch.uint8, device=dev)
+    layers = kf.make_layers(cw.kinds, cw.pos)
+    params = kf.make_params(cw.bz)
+
+    def sync_one(e):
+        n = int(cw.event_sizes[e])
+        si, ci, qi, hi_, hci = ev_in[e]
+        so, co, sto = ev_out[e]
+        d_state[:6 * n].copy_(si.view(-1), non_blocking=True)
+        d_cov[:21 * n].copy_(ci.view(-1), non_blocking=True)
+        d_q[:n].copy_(qi, non_blocking=True)
+        d_hits[:3 * n * L].copy_(hi_.view(-1), non_blocking=True)
+        d_hc[:6 * n * L].copy_(hci.view(-1), non_blocking=True)
+        kf.kf_kalman_chain(params, kf.make_layout(kf.KF_SOA, 0, n), d_state[:6 * n],
+                           d_cov[:21 * n], d_q[:n], d_hits[:3 * n * L], d_hc[:6 * n * L], layers,
+                           d_status[:n])
+        so.view(-1).copy_(d_state[:6 * n], non_blocking=True)
+        co.view(-1).copy_(d_cov[:21 * n], non_blocking=True)
+        sto.copy_(d_status[:n], non_blocking=True)
+        torch.cuda.synchronize()
+
+    for e in range(16):
+        sync_one(e)
+    results = []
+    for arrivals, served in runs:
+        lat = []
+        t0 = time.perf_counter()
+        for k in range(total):
+            arr = t0 + arrivals[k]
+            dt = arr - time.perf_counter()
+            if dt > 0:
+                time.sleep(dt)
+            sync_one(order[k])
+            lat.append((time.perf_counter() - arr) * 1e3)
+        t_end = time.perf_counter()
+        lat = np.sort(np.array(lat))
+        sync = {"tracks_per_s": tracks / (t_end - t0), "p50_ms": float(np.percentile(lat, 50)),
+                "p99_ms": float(np.percentile(lat, 99)), "max_ms": float(lat[-1])}
+        results.append({"rate_events_per_s": served["rate_events_per_s"],
+                         "continuous_batching": served, "per_event_sync": sync})
+    return {"workload": f"{total} events per rate (Poisson) cycled from 256 lognormal events "
+                        f"(median 5000 tracks), {L}-layer chain", "tracks": tracks,
+            "by_rate": results, "latency": "arrival to results in host memory; "
+            "server latency counted from submit (= arrival: the producer never waits)"}
 
 
 def main():
@@ -366,6 +525,12 @@ def main():
     kf.kf_set_step_kernel(modes[chosen_kernel])
     kind, width = layouts[chosen]
     sets = [kf.upload(w, kind, width, dev) for _ in range(4)]
+    tuned = None
+    if args.step_kernel == "auto":
+        # the library's autotuner on the chosen layout (its choice serves the
+        # timed launches through KF_STEP_AUTO)
+        kf.kf_set_step_kernel(kf.KF_STEP_AUTO)
+        tuned = kf.autotune_step(sets[0])
 
     # Capture one launch per buffer set in a CUDA graph; replay it.
     stream = torch.cuda.Stream()
@@ -441,9 +606,33 @@ def main():
            "ms_per_step": e2e_ms, "host_memory": "pinned"}
     del hb
 
+    # Update variants and the compressed covariance store on the same batch
+    # (context for the precision study; errors are measured by the tests).
+    variants = {}
+    if not args.no_variants:
+        for vname, prec in (("fp32", kf.KF_FP32), ("fp64_update", kf.KF_FP64_UPDATE),
+                            ("joseph", kf.KF_JOSEPH), ("fp64", kf.KF_FP64),
+                            ("adaptive", kf.KF_ADAPTIVE)):
+            sets[0].run(prec)
+            torch.cuda.synchronize()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            for i in range(100):
+                sets[i % len(sets)].run(prec)
+            b.record()
+            torch.cuda.synchronize()
+            ms = a.elapsed_time(b) / 100
+            variants[vname] = {"ms": ms, "tracks_per_s": w.n / (ms * 1e-3),
+                               "GBps": BYTES_PER_TRACK_P2R * w.n / (ms * 1e-3) / 1e9}
+        variants["compressed_fp32"] = compressed_bench(kf, W, w, dev, kind, width)
+
     chain = None
     if not args.no_chain:
         chain = chain_bench(args, kf, W, dev, rank)
+
+    serving = None
+    if not args.no_serving:
+        serving = serving_bench(args, kf, W, dev, rank)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -456,7 +645,8 @@ def main():
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic",
             "config": {"workload": workload_name(), "tracks": w.n, "layout": chosen,
-                       "step_kernel": chosen_kernel,
+                       "step_kernel": (f"{tuned['step_kernel']} (autotuned: {tuned})"
+                                       if tuned else chosen_kernel),
                        "precision": "fp32 standard-form update",
                        "l2": "inputs 139 MB + outputs 104 MB per step (> 126 MB L2), "
                              "rotated over 4 buffer sets",
@@ -465,12 +655,15 @@ def main():
                          "frac": achieved / peak, "traffic": traffic,
                          "peak_source": peak_src,
                          "bytes_per_track": BYTES_PER_TRACK_P2R},
+            "variants": variants,
             "chain": chain,
+            "serving": serving,
             "cpu_baseline": cpu,
             "e2e": e2e,
             "gpu_launches": args.steps,
             "clocks": clocks,
             "sweep": sweep,
+            "autotune": tuned,
             "device_error": kf.kf_take_device_error(),
         }
         print(json.dumps(line), flush=True)

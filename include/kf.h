@@ -88,10 +88,29 @@ typedef struct {
 #define KF_FP32           0 /* all arithmetic in FP32                       */
 #define KF_FP64_UPDATE    1 /* FP32 propagation; S^-1, K and C'' in FP64     */
 #define KF_JOSEPH         2 /* FP32, Joseph-form C'' = (I-KH)C'(I-KH)^T+KVK^T */
+#define KF_FP64           3 /* every operation of the step in FP64           */
+#define KF_ADAPTIVE       4 /* FP32, and the whole step redone in FP64 for a
+                               track whose FP32 step is ill-conditioned: the
+                               hit shrinks a measured variance by more than
+                               1e4, or a cylinder is crossed at an incidence
+                               cosine below 0.2.  There the covariance update
+                               C' - K H C' loses more digits than FP32 holds
+                               (the propagated covariance is rounded element
+                               by element, which breaks the near-perfect
+                               correlations the update divides out).  Other
+                               tracks run at the FP32 cost.  The single-step
+                               entry points on device arrays (and the
+                               compressed one) need a status array with it:
+                               the FP32 kernel marks ill-conditioned tracks
+                               there and a second, short kernel redoes just
+                               those (KF_ERR_ARG when status is NULL).  The
+                               host-array entry points, the chain and the
+                               server take it without that restriction.     */
 
 typedef struct {
     float    bz;        /* field along +z in tesla                          */
-    int32_t  precision; /* KF_FP32, KF_FP64_UPDATE or KF_JOSEPH             */
+    int32_t  precision; /* KF_FP32, KF_FP64_UPDATE, KF_JOSEPH, KF_FP64 or
+                           KF_ADAPTIVE                                      */
     uint32_t flags;     /* reserved, must be 0                              */
 } kf_params;
 
@@ -107,7 +126,8 @@ typedef struct {
  *   hit_cov         [6 comps] packed 3x3 hit covariance (xx, xy, yy used)
  *   z_surf          plane position(s): z_surf[0] for every track when
  *                   surf_per_track == 0, else z_surf[i] (plain [n] array)
- *   status          [n] uint8 per-track status bits, or NULL
+ *   status          [n] uint8 per-track status bits, or NULL (not NULL
+ *                   with KF_ADAPTIVE)
  *   stream          cudaStream_t
  * A track with |cos(theta)| <= 1e-4 is treated as parallel to the plane
  * (KF_NO_INTERSECT).
@@ -300,6 +320,52 @@ int kf_propagate_update_host_noalloc(int32_t kind, const kf_params *params,
                                      const float *surf, int32_t surf_per_track,
                                      uint8_t *status, int64_t chunk_tracks,
                                      void *stream);
+
+/* -------------------------------------------------------------- tuning */
+/*
+ * The autotuner measures candidate launch shapes on the caller's arrays and
+ * keeps the fastest per (GPU model, operation, kind, precision, layout,
+ * n bucket = floor(log2 n)); later calls in KF_STEP_AUTO mode use it.  No
+ * paper counterpart (the paper fixes bsize and launch shapes by hand).
+ * Single-step candidates: one thread per track with 128 or 256 threads per
+ * CTA; for AoSoA also the persistent staged kernel with 1 or 2 CTAs per SM.
+ * Chain candidates: 64, 128 or 256 threads per CTA.
+ */
+typedef struct {
+    int32_t step_kernel;  /* KF_STEP_DIRECT or KF_STEP_STAGED               */
+    int32_t threads;      /* threads per CTA (one-thread-per-track kernels) */
+    int32_t ctas_per_sm;  /* persistent CTAs per SM (staged kernel)         */
+    float   ms;           /* measured time per call of the chosen shape     */
+} kf_tuning;
+
+/* Time every candidate (3 warm-up + 10 timed calls each, synchronous) with
+ * the arguments of kf_p2z/p2r_propagate_update, store and return the best.
+ * Outputs are written repeatedly; with in == out the step is applied more
+ * than once, so pass separate output arrays. */
+int kf_autotune_step(int32_t kind, const kf_params *params, kf_layout layout,
+                     const float *state_in, const float *cov_in,
+                     float *state_out, float *cov_out, const int8_t *charge,
+                     const float *hit, const float *hit_cov, const float *surf,
+                     int32_t surf_per_track, uint8_t *status, void *stream,
+                     kf_tuning *out);
+
+/* The same for kf_kalman_chain (1 warm-up + 3 timed calls per candidate).
+ * The chain runs in place, so the start state is saved into the caller's
+ * device arrays state_scratch / cov_scratch (same sizes as state / cov),
+ * restored before every call and once more at the end: state and cov are
+ * unchanged when the call returns. */
+int kf_autotune_chain(const kf_params *params, kf_layout layout, float *state,
+                      float *cov, const int8_t *charge, const float *hits,
+                      const float *hit_covs, const kf_layer *layers, int32_t L,
+                      uint8_t *status, float *state_scratch, float *cov_scratch,
+                      void *stream, kf_tuning *out);
+
+/* The cache as text, one entry per line (*len = bytes without the final
+ * NUL; buf may be NULL to ask for the size), and back.  Entries name the GPU
+ * model, so a file written on one GB300 serves another. */
+int kf_autotune_export(char *buf, int64_t cap, int64_t *len);
+int kf_autotune_import(const char *text);
+int kf_autotune_clear(void);
 
 /* ----------------------------------------------------- the serving loop */
 /*

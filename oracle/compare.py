@@ -14,10 +14,7 @@ Cartesian (x, y) block is singular along a direction set by the crossing
 angle; an element such as C_xx = sin^2(a) C_tt is then as sensitive to a as
 1/a.  For such tracks the covariances are compared in the surface frame
 (t, r, z, k, phi, theta) of the oracle's crossing point, where the radial
-row is compared against the tangential scale.  Optionally an absolute floor
-eps_floor * sqrt(P_ii P_jj) is added, P being the oracle's covariance before
-the update: the update subtracts quantities of that scale, so no FP32
-computation can be closer than a few units of 2^-24 times it.
+row is compared against the tangential scale.
 """
 from __future__ import annotations
 
@@ -79,20 +76,13 @@ def surface_frame(cov: np.ndarray, angle: np.ndarray) -> np.ndarray:
     return pack(np.einsum("nij,njk,nlk->nil", Q, C, Q))
 
 
-def cov_errors_frame(g: np.ndarray, o: np.ndarray, angle: np.ndarray,
-                     prior: np.ndarray = None, eps_floor: float = 0.0) -> np.ndarray:
+def cov_errors_frame(g: np.ndarray, o: np.ndarray, angle: np.ndarray) -> np.ndarray:
     """Covariance errors in the surface frame at `angle` (radial row judged on
-    the tangential scale), with an optional absolute floor from `prior`."""
+    the tangential scale)."""
     gf, of = surface_frame(g, angle), surface_frame(o, angle)
     diag = of[:, _DIAG].copy()
     diag[:, 1] = diag[:, 0]  # the radial variance is structurally zero
     scale = np.stack([np.sqrt(np.abs(diag[:, i] * diag[:, j])) for i, j in _TRI], axis=1)
-    if prior is not None and eps_floor > 0.0:
-        pf = surface_frame(prior, angle)
-        pd = pf[:, _DIAG].copy()
-        pd[:, 1] = pd[:, 0]
-        pscale = np.stack([np.sqrt(np.abs(pd[:, i] * pd[:, j])) for i, j in _TRI], axis=1)
-        scale = scale + eps_floor / TOL_COV * pscale
     d = np.abs(gf - of)
     with np.errstate(divide="ignore", invalid="ignore"):
         return np.where(scale > 0, d / np.where(scale > 0, scale, 1.0), np.where(d == 0, 0.0, np.inf))
@@ -108,11 +98,11 @@ def summary(err: np.ndarray) -> dict:
 
 def compare(g_state, g_cov, g_status, o_state, o_cov, o_status,
             tol_param: float = TOL_PARAM, tol_cov: float = TOL_COV,
-            on_cylinder=None, prior=None, eps_floor: float = 0.0) -> dict:
+            on_cylinder=None) -> dict:
     """All arrays per track ([n, 6], [n, 21], [n]).  Returns a report dict with
     'ok', error summaries per component and the status agreement.
     on_cylinder: bool [n], tracks whose covariances are compared in the
-    surface frame of the oracle's point; prior/eps_floor: see module doc."""
+    surface frame of the oracle's point."""
     g_status = np.asarray(g_status).astype(np.int64)
     o_status = np.asarray(o_status).astype(np.int64)
     pe = param_errors(g_state, o_state)
@@ -121,8 +111,7 @@ def compare(g_state, g_cov, g_status, o_state, o_cov, o_status,
         m = np.asarray(on_cylinder, dtype=bool)
         os_ = np.asarray(o_state, dtype=np.float64)
         ang = np.arctan2(os_[m, 1], os_[m, 0])
-        pr = None if prior is None else np.asarray(prior)[m]
-        ce[m] = cov_errors_frame(np.asarray(g_cov)[m], np.asarray(o_cov)[m], ang, pr, eps_floor)
+        ce[m] = cov_errors_frame(np.asarray(g_cov)[m], np.asarray(o_cov)[m], ang)
     status_equal = bool(np.array_equal(g_status, o_status))
     rep = {
         "n": int(len(o_status)),

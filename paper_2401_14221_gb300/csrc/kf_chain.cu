@@ -75,7 +75,7 @@ extern "C" int kf_kalman_chain(const kf_params *params, kf_layout layout, float 
   clear_error();
   if (!params) return set_error(KF_ERR_ARG, "params is NULL");
   if (params->flags != 0) return set_error(KF_ERR_ARG, "params->flags must be 0");
-  if (params->precision < KF_FP32 || params->precision > KF_JOSEPH)
+  if (params->precision < KF_FP32 || params->precision > KF_ADAPTIVE)
     return set_error(KF_ERR_ARG, "unknown precision %d", params->precision);
   LayoutDesc d;
   if (int rc = check_layout(layout, &d)) return rc;
@@ -115,14 +115,23 @@ extern "C" int kf_kalman_chain(const kf_params *params, kf_layout layout, float 
   a.lw = d.lw;
   a.bz = params->bz;
   a.L = L;
-  const int threads = 256;
+  LaunchConfig cfg{KF_STEP_DIRECT, 256, 0};
+  if (const LaunchConfig *o = thread_override()) {
+    cfg = *o;
+  } else {
+    LaunchConfig t;
+    if (tune_lookup(kOpChain, 0, params->precision, d.soa, d.lw, d.n, &t)) cfg = t;
+  }
+  const int threads = (cfg.threads == 128 || cfg.threads == 64) ? cfg.threads : 256;
   const int64_t blocks = (d.n + threads - 1) / threads;
   if (blocks > 0x7fffffffLL) return set_error(KF_ERR_ARG, "n too large for one launch");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   switch (params->precision) {
     case KF_FP32: chain_kernel<kFP32><<<(unsigned)blocks, threads, 0, s>>>(a); break;
     case KF_FP64_UPDATE: chain_kernel<kFP64Update><<<(unsigned)blocks, threads, 0, s>>>(a); break;
-    default: chain_kernel<kJoseph><<<(unsigned)blocks, threads, 0, s>>>(a); break;
+    case KF_JOSEPH: chain_kernel<kJoseph><<<(unsigned)blocks, threads, 0, s>>>(a); break;
+    case KF_FP64: chain_kernel<kFP64><<<(unsigned)blocks, threads, 0, s>>>(a); break;
+    default: chain_kernel<kAdaptive><<<(unsigned)blocks, threads, 0, s>>>(a); break;
   }
   return check_cuda(cudaGetLastError(), "chain launch");
 }

@@ -56,9 +56,9 @@ __device__ __forceinline__ unsigned chain_track(float (&p)[6], float (&C)[21], f
     const LayerHit h = next;
     if (l + 1 < L) load_layer_hit(hits, hit_stride, hitcovs, hc_stride, l + 1, l3, l6, next);
     if (kinds[l] == kP2z)
-      st |= p2z_step<VARIANT>(p, C, qf, bz, pos[l], h.hx, h.hy, h.hc[0], h.hc[1], h.hc[2]);
+      st |= p2z_step_inplace<VARIANT>(p, C, qf, bz, pos[l], h.hx, h.hy, h.hc[0], h.hc[1], h.hc[2]);
     else
-      st |= p2r_step<VARIANT>(p, C, qf, bz, pos[l], h.hx, h.hy, h.hz, h.hc);
+      st |= p2r_step_inplace<VARIANT>(p, C, qf, bz, pos[l], h.hx, h.hy, h.hz, h.hc);
   }
   return st;
 }

@@ -123,7 +123,7 @@ int run_host(int kind, const kf_params *params, kf_layout layout, const float *s
   clear_error();
   if (!params) return set_error(KF_ERR_ARG, "params is NULL");
   if (params->flags != 0) return set_error(KF_ERR_ARG, "params->flags must be 0");
-  if (params->precision < KF_FP32 || params->precision > KF_JOSEPH)
+  if (params->precision < KF_FP32 || params->precision > KF_ADAPTIVE)
     return set_error(KF_ERR_ARG, "unknown precision %d", params->precision);
   LayoutDesc d;
   if (int rc = check_layout(layout, &d)) return rc;
@@ -179,7 +179,7 @@ int run_host(int kind, const kf_params *params, kf_layout layout, const float *s
                           surf_per_track ? 4 * m : 4, cudaMemcpyDefault, s);
     if (int rc = check_cuda(e, "host-to-device copy")) return rc;
     StepArgs a{d_st_in, d_cv_in, d_st_out, d_cv_out, d_q,  d_hit, d_hc, d_surf,
-               status ? d_status : nullptr, m, dc.soa, dc.lw, params->bz, surf_per_track};
+               (status || params->precision == KF_ADAPTIVE) ? d_status : nullptr, m, dc.soa, dc.lw, params->bz, surf_per_track};
     if (int rc = launch_step_kernel(kind, params->precision, a, s)) return rc;
     e = copy_chunk(state_out, d_st_out, 6, d, c0, m, false, s);
     if (e == cudaSuccess) e = copy_chunk(cov_out, d_cv_out, 21, d, c0, m, false, s);

@@ -118,7 +118,7 @@ extern "C" int kf_propagate_update_host_noalloc(int32_t kind, const kf_params *p
     return set_error(KF_ERR_ARG, "kind = %d is neither KF_P2Z nor KF_P2R", kind);
   if (!params) return set_error(KF_ERR_ARG, "params is NULL");
   if (params->flags != 0) return set_error(KF_ERR_ARG, "params->flags must be 0");
-  if (params->precision < KF_FP32 || params->precision > KF_JOSEPH)
+  if (params->precision < KF_FP32 || params->precision > KF_ADAPTIVE)
     return set_error(KF_ERR_ARG, "unknown precision %d", params->precision);
   LayoutDesc d;
   if (int rc = check_layout(layout, &d)) return rc;
@@ -170,7 +170,7 @@ extern "C" int kf_propagate_update_host_noalloc(int32_t kind, const kf_params *p
                           cudaMemcpyDefault, s);
     if (int rc = check_cuda(e, "host-to-device copy into the staging buffer")) return rc;
     StepArgs a{d_st_in, d_cv_in, d_st_out, d_cv_out, d_q, d_hit, d_hc, d_surf,
-               status ? d_status : nullptr, m, dc.soa, dc.lw, params->bz, surf_per_track};
+               (status || params->precision == KF_ADAPTIVE) ? d_status : nullptr, m, dc.soa, dc.lw, params->bz, surf_per_track};
     if (int rc = launch_step_kernel(kind, params->precision, a, s)) return rc;
     e = stage_copy(state_out, d_st_out, 6, d, c0, m, false, s);
     if (e == cudaSuccess) e = stage_copy(cov_out, d_cv_out, 21, d, c0, m, false, s);

@@ -32,7 +32,7 @@ __device__ __forceinline__ Loc locate(int64_t i, int64_t n, int32_t soa, int32_t
 }
 
 template <int KIND, int VARIANT>
-__global__ void __launch_bounds__(256) step_kernel(const StepArgs a) {
+__global__ void __launch_bounds__(256) step_kernel(const __grid_constant__ StepArgs a) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= a.n) return;
   const Loc l6 = locate<6>(i, a.n, a.soa, a.lw);
@@ -64,6 +64,12 @@ __global__ void __launch_bounds__(256) step_kernel(const StepArgs a) {
     for (int c = 0; c < 6; ++c) hc[c] = __ldg(a.hitcov + l6.base + c * l6.stride);
     st = p2r_step<VARIANT>(p, C, qf, a.bz, surf, hx, hy, hz, hc);
   }
+  if constexpr (VARIANT == kAdaptive) {
+    if (st & kRedo) {  // ill-conditioned in FP32: left to the FP64 redo pass
+      a.status[i] = (uint8_t)kRedo;
+      return;
+    }
+  }
   st |= finite_status(p, C);
 
 #pragma unroll
@@ -71,6 +77,26 @@ __global__ void __launch_bounds__(256) step_kernel(const StepArgs a) {
 #pragma unroll
   for (int e = 0; e < 21; ++e) __stcs(a.cov_out + l21.base + e * l21.stride, C[e]);
   if (a.status) a.status[i] = (uint8_t)st;
+}
+
+// The redo pass of KF_ADAPTIVE: a grid-stride scan of the status bytes (a
+// warp reads 32 consecutive bytes); marked tracks run the FP64 step.
+template <int KIND>
+__global__ void __launch_bounds__(256) redo_pass_kernel(const __grid_constant__ StepArgs a) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += stride)
+    if (a.status[i] & kRedo) a.status[i] = (uint8_t)redo_track_fp64<KIND>(a, i);
+}
+
+int launch_redo_pass(int kind, const StepArgs &a, cudaStream_t s) {
+  if (a.n == 0) return KF_OK;
+  const int64_t blocks = (a.n + 255) / 256;
+  const unsigned g = (unsigned)(blocks < 1024 ? blocks : 1024);
+  if (kind == kP2z)
+    redo_pass_kernel<kP2z><<<g, 256, 0, s>>>(a);
+  else
+    redo_pass_kernel<kP2r><<<g, 256, 0, s>>>(a);
+  return check_cuda(cudaGetLastError(), "adaptive redo pass launch");
 }
 
 template <int KIND>
@@ -82,7 +108,7 @@ static int launch_step(const kf_params *params, kf_layout layout, const float *s
   clear_error();
   if (!params) return set_error(KF_ERR_ARG, "params is NULL");
   if (params->flags != 0) return set_error(KF_ERR_ARG, "params->flags must be 0");
-  if (params->precision < KF_FP32 || params->precision > KF_JOSEPH)
+  if (params->precision < KF_FP32 || params->precision > KF_ADAPTIVE)
     return set_error(KF_ERR_ARG, "unknown precision %d", params->precision);
   LayoutDesc d;
   if (int rc = check_layout(layout, &d)) return rc;
@@ -105,6 +131,8 @@ static int launch_step(const kf_params *params, kf_layout layout, const float *s
       if (int rc = check_device_range(ptrs[k], bytes[k], names[k])) return rc;
     if (status)
       if (int rc = check_device_range(status, d.n, "status")) return rc;
+    if (!status && params->precision == KF_ADAPTIVE)
+      return set_error(KF_ERR_ARG, "KF_ADAPTIVE needs a status array (its redo pass reads it)");
   }
   if (partial_overlap(state_in, 4 * layout_floats(d, 6), state_out, 4 * layout_floats(d, 6)) ||
       partial_overlap(cov_in, 4 * layout_floats(d, 21), cov_out, 4 * layout_floats(d, 21)))
@@ -121,13 +149,33 @@ std::atomic<int> g_step_mode{KF_STEP_AUTO};
 
 int step_kernel_mode() { return g_step_mode.load(std::memory_order_relaxed); }
 
+static int launch_step_main(int kind, int precision, const StepArgs &a, cudaStream_t s);
+
 int launch_step_kernel(int kind, int precision, const StepArgs &a, cudaStream_t s) {
   if (a.n == 0) return KF_OK;
-  // AoSoA tiles are contiguous runs: stage them with bulk copies unless the
-  // direct kernel was asked for.
-  if (!a.soa && step_kernel_mode() != KF_STEP_DIRECT)
-    return launch_step_staged(kind, precision, a, s);
-  const int threads = 256;
+  if (precision == KF_ADAPTIVE && !a.status)
+    return set_error(KF_ERR_ARG, "KF_ADAPTIVE needs a status array (its redo pass reads it)");
+  if (int rc = launch_step_main(kind, precision, a, s)) return rc;
+  return precision == KF_ADAPTIVE ? launch_redo_pass(kind, a, s) : KF_OK;
+}
+
+static int launch_step_main(int kind, int precision, const StepArgs &a, cudaStream_t s) {
+  LaunchConfig cfg{a.soa ? KF_STEP_DIRECT : KF_STEP_STAGED, 256, 2};
+  if (const LaunchConfig *o = thread_override()) {
+    cfg = *o;
+  } else {
+    const int mode = step_kernel_mode();
+    if (mode == KF_STEP_DIRECT) {
+      cfg.kernel = KF_STEP_DIRECT;
+    } else if (mode == KF_STEP_AUTO) {
+      LaunchConfig t;
+      if (tune_lookup(kOpStep, kind, precision, a.soa, a.lw, a.n, &t)) cfg = t;
+    }
+  }
+  // AoSoA tiles are contiguous runs: stage them with bulk copies.
+  if (!a.soa && cfg.kernel == KF_STEP_STAGED)
+    return launch_step_staged(kind, precision, a, s, cfg.ctas_per_sm);
+  const int threads = (cfg.threads == 128 || cfg.threads == 64) ? cfg.threads : 256;
   const int64_t blocks = (a.n + threads - 1) / threads;
   if (blocks > 0x7fffffffLL) return set_error(KF_ERR_ARG, "n too large for one launch");
   const unsigned g = (unsigned)blocks;
@@ -135,13 +183,17 @@ int launch_step_kernel(int kind, int precision, const StepArgs &a, cudaStream_t 
     switch (precision) {
       case KF_FP32: step_kernel<kP2z, kFP32><<<g, threads, 0, s>>>(a); break;
       case KF_FP64_UPDATE: step_kernel<kP2z, kFP64Update><<<g, threads, 0, s>>>(a); break;
-      default: step_kernel<kP2z, kJoseph><<<g, threads, 0, s>>>(a); break;
+      case KF_JOSEPH: step_kernel<kP2z, kJoseph><<<g, threads, 0, s>>>(a); break;
+      case KF_FP64: step_kernel<kP2z, kFP64><<<g, threads, 0, s>>>(a); break;
+      default: step_kernel<kP2z, kAdaptive><<<g, threads, 0, s>>>(a); break;
     }
   } else {
     switch (precision) {
       case KF_FP32: step_kernel<kP2r, kFP32><<<g, threads, 0, s>>>(a); break;
       case KF_FP64_UPDATE: step_kernel<kP2r, kFP64Update><<<g, threads, 0, s>>>(a); break;
-      default: step_kernel<kP2r, kJoseph><<<g, threads, 0, s>>>(a); break;
+      case KF_JOSEPH: step_kernel<kP2r, kJoseph><<<g, threads, 0, s>>>(a); break;
+      case KF_FP64: step_kernel<kP2r, kFP64><<<g, threads, 0, s>>>(a); break;
+      default: step_kernel<kP2r, kAdaptive><<<g, threads, 0, s>>>(a); break;
     }
   }
   return check_cuda(cudaGetLastError(), kind == kP2z ? "p2z step launch" : "p2r step launch");

@@ -5,6 +5,8 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 
+#include "kf_device.cuh"
+
 namespace kf {
 
 // Device pointers and sizes for one single-step launch (already validated).
@@ -25,14 +27,93 @@ struct StepArgs {
   int32_t surf_per_track;
 };
 
+#ifdef __CUDACC__
+// The kAdaptive redo of track i of a step launch: read its inputs from
+// global memory, run the step in double, write its outputs there and return
+// its status (finite check included).  Used by the redo pass, a kernel of its
+// own, so that the FP32 kernel's registers never carry the FP64 step.  In
+// place is safe: the FP32 kernel did not store this track's result.
+template <int KIND>
+__device__ __forceinline__ unsigned redo_track_fp64(const StepArgs &a, int64_t i) {
+  int64_t b6, b21, b3, s;
+  if (a.soa) {
+    b6 = b21 = b3 = i;
+    s = a.n;
+  } else {
+    const int64_t W = int64_t(1) << a.lw, blk = i >> a.lw, r = i & (W - 1);
+    b6 = blk * 6 * W + r;
+    b21 = blk * 21 * W + r;
+    b3 = blk * 3 * W + r;
+    s = W;
+  }
+  double p[6], C[21], hc[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0}, shrink, cinc;
+#pragma unroll
+  for (int c = 0; c < 6; ++c) p[c] = a.state_in[b6 + c * s];
+#pragma unroll
+  for (int e = 0; e < 21; ++e) C[e] = a.cov_in[b21 + e * s];
+  constexpr int nhc = KIND == kP2z ? 3 : 6;
+#pragma unroll
+  for (int c = 0; c < nhc; ++c) hc[c] = a.hitcov[b6 + c * s];
+  const double qf = a.charge[i];
+  const double surf = a.surf[a.surf_per_track ? i : 0];
+  const double hx = a.hit[b3], hy = a.hit[b3 + s];
+  unsigned st;
+  if (KIND == kP2z)
+    st = p2z_step_t<double, kStandard>(p, C, qf, (double)a.bz, surf, hx, hy, hc[0], hc[1], hc[2],
+                                       shrink);
+  else
+    st = p2r_step_t<double, kStandard>(p, C, qf, (double)a.bz, surf, hx, hy,
+                                       (double)a.hit[b3 + 2 * s], hc, shrink, cinc);
+  // exact when the track was not propagated (float -> double -> float)
+  float pf[6], Cf[21];
+#pragma unroll
+  for (int c = 0; c < 6; ++c) pf[c] = (float)p[c];
+#pragma unroll
+  for (int e = 0; e < 21; ++e) Cf[e] = (float)C[e];
+  st |= finite_status(pf, Cf);
+#pragma unroll
+  for (int c = 0; c < 6; ++c) __stcs(a.state_out + b6 + c * s, pf[c]);
+#pragma unroll
+  for (int e = 0; e < 21; ++e) __stcs(a.cov_out + b21 + e * s, Cf[e]);
+  return st;
+}
+#endif
+
+// How a step (or chain) launch is shaped.
+struct LaunchConfig {
+  int kernel;       // KF_STEP_DIRECT or KF_STEP_STAGED
+  int threads;      // CTA size of the one-thread-per-track kernels
+  int ctas_per_sm;  // persistent CTAs per SM of the staged kernel
+};
+
 // Launch the p2z (kind 0) or p2r (kind 1) step kernel for `a` on stream s
-// with the given KF_FP32 / KF_FP64_UPDATE / KF_JOSEPH variant.
+// with the given KF_* precision variant.  The shape comes from, in order:
+// the autotuner's per-thread override while it measures, the process-wide
+// kf_set_step_kernel mode, the tuning cache, the defaults.
 int launch_step_kernel(int kind, int precision, const StepArgs &a, cudaStream_t s);
 
+// Second pass of KF_ADAPTIVE: redo in FP64 every track whose status the
+// step kernel marked with kRedo (those tracks' outputs are not yet written).
+int launch_redo_pass(int kind, const StepArgs &a, cudaStream_t s);
+
 // The persistent bulk-async-staged kernel (AoSoA layouts only).
-int launch_step_staged(int kind, int precision, const StepArgs &a, cudaStream_t s);
+int launch_step_staged(int kind, int precision, const StepArgs &a, cudaStream_t s,
+                       int ctas_per_sm);
 
 // Process-wide choice between the kernels: KF_STEP_AUTO / _DIRECT / _STAGED.
 int step_kernel_mode();
+
+// ------------------------------------------------------------- tuning
+enum TuneOp : int { kOpStep = 0, kOpChain = 1 };
+
+// Shape forced on the calling thread's launches (the autotuner sets it
+// while it measures candidates); nullptr when none.
+const LaunchConfig *thread_override();
+void set_thread_override(const LaunchConfig *cfg);
+
+// Cached best shape for (current device, op, kind, precision, layout, n).
+bool tune_lookup(int op, int kind, int precision, int soa, int lw, int64_t n, LaunchConfig *out);
+void tune_store(int op, int kind, int precision, int soa, int lw, int64_t n,
+                const LaunchConfig &cfg, float ms);
 
 }  // namespace kf

@@ -60,28 +60,69 @@ __device__ __forceinline__ constexpr int od_col(int k) {
   return k - (od_row(k) * (od_row(k) - 1)) / 2;
 }
 
+// Load track i: state, and the covariance decoded from sigma / rho
+// (C_ii = sigma_i^2, C_ij = rho_ij sigma_i sigma_j).
+template <class T>
+__device__ __forceinline__ void load_compressed(const CompressedArgs &a, const Loc &l6,
+                                                const Loc &l15, T (&p)[6], T (&C)[21]) {
+  float sg[6];
+#pragma unroll
+  for (int c = 0; c < 6; ++c) p[c] = __ldg(a.state_in + l6.base + c * l6.stride);
+#pragma unroll
+  for (int c = 0; c < 6; ++c) sg[c] = __ldg(a.sigma_in + l6.base + c * l6.stride);
+#pragma unroll
+  for (int c = 0; c < 6; ++c) C[tri(c, c)] = T(sg[c] * sg[c]);
+#pragma unroll
+  for (int k = 0; k < 15; ++k)
+    C[tri(od_row(k), od_col(k))] =
+        T(__half2float(a.rho_in[l15.base + k * l15.stride]) * sg[od_row(k)] * sg[od_col(k)]);
+}
+
+// Encode and store track i's result; a track that was not propagated gets
+// its input sigma / rho back bit for bit.
+__device__ __forceinline__ void store_compressed(const CompressedArgs &a, const Loc &l6,
+                                                 const Loc &l15, const float (&p)[6],
+                                                 const float (&C)[21], unsigned st) {
+  float sg[6];
+  __half rh[15];
+  if (!(st & kNoIntersect)) {
+    // sigma_i = sqrt(C_ii), rho_ij = C_ij / (sigma_i sigma_j) in [-1, 1]
+    float inv[6];
+#pragma unroll
+    for (int c = 0; c < 6; ++c) {
+      sg[c] = sqrtf(fmaxf(C[tri(c, c)], 0.0f));
+      inv[c] = sg[c] > 0.0f ? 1.0f / sg[c] : 0.0f;
+    }
+#pragma unroll
+    for (int k = 0; k < 15; ++k) {
+      const float r = C[tri(od_row(k), od_col(k))] * inv[od_row(k)] * inv[od_col(k)];
+      rh[k] = __float2half_rn(fminf(fmaxf(r, -1.0f), 1.0f));
+    }
+  } else {
+#pragma unroll
+    for (int c = 0; c < 6; ++c) sg[c] = __ldg(a.sigma_in + l6.base + c * l6.stride);
+#pragma unroll
+    for (int k = 0; k < 15; ++k) rh[k] = a.rho_in[l15.base + k * l15.stride];
+  }
+#pragma unroll
+  for (int c = 0; c < 6; ++c) __stcs(a.state_out + l6.base + c * l6.stride, p[c]);
+#pragma unroll
+  for (int c = 0; c < 6; ++c) __stcs(a.sigma_out + l6.base + c * l6.stride, sg[c]);
+#pragma unroll
+  for (int k = 0; k < 15; ++k) a.rho_out[l15.base + k * l15.stride] = rh[k];
+}
+
 template <int KIND, int VARIANT>
-__global__ void __launch_bounds__(256) step_compressed_kernel(const CompressedArgs a) {
+__global__ void __launch_bounds__(256)
+    step_compressed_kernel(const __grid_constant__ CompressedArgs a) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= a.n) return;
   const Loc l6 = locate<6>(i, a.n, a.soa, a.lw);
   const Loc l15 = locate<15>(i, a.n, a.soa, a.lw);
   const Loc l3 = locate<3>(i, a.n, a.soa, a.lw);
 
-  float p[6], sg[6], C[21];
-  __half rh[15];
-#pragma unroll
-  for (int c = 0; c < 6; ++c) p[c] = __ldg(a.state_in + l6.base + c * l6.stride);
-#pragma unroll
-  for (int c = 0; c < 6; ++c) sg[c] = __ldg(a.sigma_in + l6.base + c * l6.stride);
-#pragma unroll
-  for (int k = 0; k < 15; ++k) rh[k] = a.rho_in[l15.base + k * l15.stride];
-  // decode: C_ii = sigma_i^2, C_ij = rho_ij sigma_i sigma_j
-#pragma unroll
-  for (int c = 0; c < 6; ++c) C[tri(c, c)] = sg[c] * sg[c];
-#pragma unroll
-  for (int k = 0; k < 15; ++k)
-    C[tri(od_row(k), od_col(k))] = __half2float(rh[k]) * sg[od_row(k)] * sg[od_col(k)];
+  float p[6], C[21];
+  load_compressed(a, l6, l15, p, C);
   const float qf = (float)__ldg(a.charge + i);
   const float surf = __ldg(a.surf + (a.surf_per_track ? i : 0));
 
@@ -102,29 +143,52 @@ __global__ void __launch_bounds__(256) step_compressed_kernel(const CompressedAr
     for (int c = 0; c < 6; ++c) hc[c] = __ldg(a.hitcov + l6.base + c * l6.stride);
     st = p2r_step<VARIANT>(p, C, qf, a.bz, surf, hx, hy, hz, hc);
   }
-  st |= finite_status(p, C);
-
-  if (!(st & kNoIntersect)) {
-    // encode: sigma_i = sqrt(C_ii), rho_ij = C_ij / (sigma_i sigma_j) in [-1, 1]
-    float inv[6];
-#pragma unroll
-    for (int c = 0; c < 6; ++c) {
-      sg[c] = sqrtf(fmaxf(C[tri(c, c)], 0.0f));
-      inv[c] = sg[c] > 0.0f ? 1.0f / sg[c] : 0.0f;
-    }
-#pragma unroll
-    for (int k = 0; k < 15; ++k) {
-      const float r = C[tri(od_row(k), od_col(k))] * inv[od_row(k)] * inv[od_col(k)];
-      rh[k] = __float2half_rn(fminf(fmaxf(r, -1.0f), 1.0f));
+  if constexpr (VARIANT == kAdaptive) {
+    if (st & kRedo) {  // ill-conditioned in FP32: left to the FP64 redo pass
+      a.status[i] = (uint8_t)kRedo;
+      return;
     }
   }
-#pragma unroll
-  for (int c = 0; c < 6; ++c) __stcs(a.state_out + l6.base + c * l6.stride, p[c]);
-#pragma unroll
-  for (int c = 0; c < 6; ++c) __stcs(a.sigma_out + l6.base + c * l6.stride, sg[c]);
-#pragma unroll
-  for (int k = 0; k < 15; ++k) a.rho_out[l15.base + k * l15.stride] = rh[k];
+  st |= finite_status(p, C);
+  store_compressed(a, l6, l15, p, C, st);
   if (a.status) a.status[i] = (uint8_t)st;
+}
+
+// KF_ADAPTIVE's second pass on the compressed store: tracks marked kRedo
+// are decoded again from their (untouched) inputs and stepped in FP64.
+template <int KIND>
+__global__ void __launch_bounds__(256)
+    redo_compressed_kernel(const __grid_constant__ CompressedArgs a) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += stride) {
+    if (!(a.status[i] & kRedo)) continue;
+    const Loc l6 = locate<6>(i, a.n, a.soa, a.lw);
+    const Loc l15 = locate<15>(i, a.n, a.soa, a.lw);
+    const Loc l3 = locate<3>(i, a.n, a.soa, a.lw);
+    double p[6], C[21], hc[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0}, shrink, cinc;
+    load_compressed(a, l6, l15, p, C);
+    constexpr int nhc = KIND == kP2z ? 3 : 6;
+#pragma unroll
+    for (int c = 0; c < nhc; ++c) hc[c] = a.hitcov[l6.base + c * l6.stride];
+    const double qf = a.charge[i];
+    const double surf = a.surf[a.surf_per_track ? i : 0];
+    const double hx = a.hit[l3.base], hy = a.hit[l3.base + l3.stride];
+    unsigned st;
+    if (KIND == kP2z)
+      st = p2z_step_t<double, kStandard>(p, C, qf, (double)a.bz, surf, hx, hy, hc[0], hc[1],
+                                         hc[2], shrink);
+    else
+      st = p2r_step_t<double, kStandard>(p, C, qf, (double)a.bz, surf, hx, hy,
+                                         (double)a.hit[l3.base + 2 * l3.stride], hc, shrink, cinc);
+    float pf[6], Cf[21];
+#pragma unroll
+    for (int c = 0; c < 6; ++c) pf[c] = (float)p[c];
+#pragma unroll
+    for (int e = 0; e < 21; ++e) Cf[e] = (float)C[e];
+    st |= finite_status(pf, Cf);
+    store_compressed(a, l6, l15, pf, Cf, st);
+    a.status[i] = (uint8_t)st;
+  }
 }
 
 }  // namespace
@@ -141,7 +205,7 @@ extern "C" int kf_propagate_update_compressed(
     return set_error(KF_ERR_ARG, "kind = %d is neither KF_P2Z nor KF_P2R", kind);
   if (!params) return set_error(KF_ERR_ARG, "params is NULL");
   if (params->flags != 0) return set_error(KF_ERR_ARG, "params->flags must be 0");
-  if (params->precision < KF_FP32 || params->precision > KF_JOSEPH)
+  if (params->precision < KF_FP32 || params->precision > KF_ADAPTIVE)
     return set_error(KF_ERR_ARG, "unknown precision %d", params->precision);
   LayoutDesc d;
   if (int rc = check_layout(layout, &d)) return rc;
@@ -162,6 +226,8 @@ extern "C" int kf_propagate_update_compressed(
     if (int rc = check_device_range(ptrs[k], bytes[k], names[k])) return rc;
   if (status)
     if (int rc = check_device_range(status, d.n, "status")) return rc;
+  if (!status && params->precision == KF_ADAPTIVE)
+    return set_error(KF_ERR_ARG, "KF_ADAPTIVE needs a status array (its redo pass reads it)");
   if (partial_overlap(state_in, b6, state_out, b6) || partial_overlap(sigma_in, b6, sigma_out, b6) ||
       partial_overlap(rho_in, b15, rho_out, b15))
     return set_error(KF_ERR_ARG, "input and output overlap without coinciding");
@@ -179,14 +245,25 @@ extern "C" int kf_propagate_update_compressed(
     switch (params->precision) {
       case KF_FP32: step_compressed_kernel<kP2z, kFP32><<<g, threads, 0, s>>>(a); break;
       case KF_FP64_UPDATE: step_compressed_kernel<kP2z, kFP64Update><<<g, threads, 0, s>>>(a); break;
-      default: step_compressed_kernel<kP2z, kJoseph><<<g, threads, 0, s>>>(a); break;
+      case KF_JOSEPH: step_compressed_kernel<kP2z, kJoseph><<<g, threads, 0, s>>>(a); break;
+      case KF_FP64: step_compressed_kernel<kP2z, kFP64><<<g, threads, 0, s>>>(a); break;
+      default: step_compressed_kernel<kP2z, kAdaptive><<<g, threads, 0, s>>>(a); break;
     }
   } else {
     switch (params->precision) {
       case KF_FP32: step_compressed_kernel<kP2r, kFP32><<<g, threads, 0, s>>>(a); break;
       case KF_FP64_UPDATE: step_compressed_kernel<kP2r, kFP64Update><<<g, threads, 0, s>>>(a); break;
-      default: step_compressed_kernel<kP2r, kJoseph><<<g, threads, 0, s>>>(a); break;
+      case KF_JOSEPH: step_compressed_kernel<kP2r, kJoseph><<<g, threads, 0, s>>>(a); break;
+      case KF_FP64: step_compressed_kernel<kP2r, kFP64><<<g, threads, 0, s>>>(a); break;
+      default: step_compressed_kernel<kP2r, kAdaptive><<<g, threads, 0, s>>>(a); break;
     }
   }
-  return check_cuda(cudaGetLastError(), "compressed step launch");
+  if (int rc = check_cuda(cudaGetLastError(), "compressed step launch")) return rc;
+  if (params->precision != KF_ADAPTIVE) return KF_OK;
+  const unsigned gr = g < 1024u ? g : 1024u;
+  if (kind == KF_P2Z)
+    redo_compressed_kernel<kP2z><<<gr, threads, 0, s>>>(a);
+  else
+    redo_compressed_kernel<kP2r><<<gr, threads, 0, s>>>(a);
+  return check_cuda(cudaGetLastError(), "compressed redo pass launch");
 }

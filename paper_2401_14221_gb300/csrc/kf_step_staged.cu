@@ -113,14 +113,20 @@ __device__ __forceinline__ void bulk_g2s(void *sdst, const void *gsrc, uint32_t 
 }
 
 template <int KIND, int VARIANT, int W>
-__global__ void __launch_bounds__(kThreads, 2) step_staged_kernel(const StepArgs a) {
+__global__ void __launch_bounds__(kThreads, 2) step_staged_kernel(const __grid_constant__ StepArgs a) {
   static_assert(kT % W == 0, "tile must hold whole AoSoA blocks");
   extern __shared__ __align__(128) unsigned char smem[];
   uint64_t *full = reinterpret_cast<uint64_t *>(smem + kStages * kStageB);
   uint64_t *empty = full + kStages;
   const int warp = threadIdx.x >> 5;
   const int lane = threadIdx.x & 31;
-  const int64_t ntiles = (a.n + kT - 1) / kT;
+  // Balanced contiguous ranges: CTA b owns tracks [begin, end), the same
+  // number of whole AoSoA blocks for every CTA, processed in tiles of kT
+  // (the last one partial), so all CTAs finish within one block of each other.
+  const int64_t per = (((a.n + gridDim.x - 1) / gridDim.x) + W - 1) / W * W;
+  const int64_t begin = (int64_t)blockIdx.x * per;
+  const int64_t end = (begin + per < a.n) ? begin + per : a.n;
+  const int64_t ntiles = (begin < end) ? (end - begin + kT - 1) / kT : 0;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < kStages; ++s) {
@@ -134,13 +140,12 @@ __global__ void __launch_bounds__(kThreads, 2) step_staged_kernel(const StepArgs
   if (warp == kComputeWarps) {
     // ------------------------------------------------------------ producer
     if (lane == 0) {
-      int k = 0;
-      for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x, ++k) {
-        const int s = k % kStages;
+      for (int64_t k = 0; k < ntiles; ++k) {
+        const int s = (int)(k % kStages);
         const uint32_t ph = (uint32_t)(k / kStages) & 1u;
         if (k >= kStages && !mbar_wait(&empty[s], ph ^ 1u)) break;
-        const int64_t first = t * kT;
-        const int64_t m = (a.n - first < kT) ? a.n - first : kT;
+        const int64_t first = begin + k * kT;
+        const int64_t m = (end - first < kT) ? end - first : kT;
         const uint32_t cols = (uint32_t)(((m + W - 1) / W) * W);  // whole blocks
         unsigned char *st = smem + s * kStageB;
         mbar_arrive_expect_tx(&full[s], cols * (6 + 21 + 3 + 6) * 4);
@@ -156,12 +161,11 @@ __global__ void __launch_bounds__(kThreads, 2) step_staged_kernel(const StepArgs
   // --------------------------------------------------------------- compute
   const int il = warp * 32 + lane;          // track within the tile
   const int blk = il / W, r = il % W;       // AoSoA block and slot within the tile
-  int k = 0;
-  for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x, ++k) {
-    const int s = k % kStages;
+  for (int64_t k = 0; k < ntiles; ++k) {
+    const int s = (int)(k % kStages);
     const uint32_t ph = (uint32_t)(k / kStages) & 1u;
-    const int64_t i = t * kT + il;
-    const bool live = i < a.n;
+    const int64_t i = begin + k * kT + il;
+    const bool live = i < end;
     // plain per-track arrays: issue before waiting on the stage
     const float qf = live ? (float)__ldg(a.charge + i) : 1.0f;
     const float surf = __ldg(a.surf + ((a.surf_per_track && live) ? i : 0));
@@ -197,10 +201,16 @@ __global__ void __launch_bounds__(kThreads, 2) step_staged_kernel(const StepArgs
       st = p2z_step<VARIANT>(p, C, qf, a.bz, surf, hx, hy, hc[0], hc[1], hc[2]);
     else
       st = p2r_step<VARIANT>(p, C, qf, a.bz, surf, hx, hy, hz, hc);
-    st |= finite_status(p, C);
-
+    if constexpr (VARIANT == kAdaptive) {
+      if (st & kRedo) {  // ill-conditioned in FP32: left to the FP64 redo pass
+        a.status[i] = (uint8_t)kRedo;
+        continue;
+      }
+    }
     const int64_t b6 = (i / W) * (6 * W) + (i % W);
     const int64_t b21 = (i / W) * (21 * W) + (i % W);
+    st |= finite_status(p, C);
+
 #pragma unroll
     for (int c = 0; c < 6; ++c) __stcs(a.state_out + b6 + c * W, p[c]);
 #pragma unroll
@@ -254,9 +264,10 @@ int sm_count(int dev, int *out) {
 
 }  // namespace staged
 
-// Persistent staged launch for AoSoA layouts: two CTAs per SM, each looping
-// over tiles blockIdx.x, blockIdx.x + gridDim.x, ...
-int launch_step_staged(int kind, int precision, const StepArgs &a, cudaStream_t s) {
+// Persistent staged launch for AoSoA layouts: one or two CTAs per SM, each
+// working through its own contiguous, equal share of whole AoSoA blocks.
+int launch_step_staged(int kind, int precision, const StepArgs &a, cudaStream_t s,
+                       int ctas_per_sm) {
   using namespace staged;
   if (a.n == 0) return KF_OK;
   if (a.soa) return set_error(KF_ERR_UNSUPPORTED, "the staged kernel takes AoSoA layouts");
@@ -264,18 +275,23 @@ int launch_step_staged(int kind, int precision, const StepArgs &a, cudaStream_t 
   if (int rc = check_cuda(cudaGetDevice(&dev), "cudaGetDevice")) return rc;
   if (int rc = sm_count(dev, &sms)) return rc;
   const int64_t ntiles = (a.n + kT - 1) / kT;
-  const int grid = (int)((ntiles < 2 * (int64_t)sms) ? ntiles : 2 * (int64_t)sms);
+  const int64_t slots = (int64_t)sms * (ctas_per_sm == 1 ? 1 : 2);
+  const int grid = (int)(ntiles < slots ? ntiles : slots);
   if (kind == kP2z) {
     switch (precision) {
       case KF_FP32: return launch_v<kP2z, kFP32>(a, s, grid, dev);
       case KF_FP64_UPDATE: return launch_v<kP2z, kFP64Update>(a, s, grid, dev);
-      default: return launch_v<kP2z, kJoseph>(a, s, grid, dev);
+      case KF_JOSEPH: return launch_v<kP2z, kJoseph>(a, s, grid, dev);
+      case KF_FP64: return launch_v<kP2z, kFP64>(a, s, grid, dev);
+      default: return launch_v<kP2z, kAdaptive>(a, s, grid, dev);
     }
   }
   switch (precision) {
     case KF_FP32: return launch_v<kP2r, kFP32>(a, s, grid, dev);
     case KF_FP64_UPDATE: return launch_v<kP2r, kFP64Update>(a, s, grid, dev);
-    default: return launch_v<kP2r, kJoseph>(a, s, grid, dev);
+    case KF_JOSEPH: return launch_v<kP2r, kJoseph>(a, s, grid, dev);
+    case KF_FP64: return launch_v<kP2r, kFP64>(a, s, grid, dev);
+    default: return launch_v<kP2r, kAdaptive>(a, s, grid, dev);
   }
 }
 

@@ -25,7 +25,7 @@ HEADER = os.path.join(os.path.dirname(_PKG), "include", "kf.h")
 KF_OK, KF_ERR_ARG, KF_ERR_CUDA, KF_ERR_UNSUPPORTED, KF_ERR_TIMEOUT = 0, 1, 2, 3, 4
 NO_INTERSECT, S_NOT_PD, BAD_K, NONFINITE = 1, 2, 4, 8
 KF_SOA, KF_AOSOA = 0, 1
-KF_FP32, KF_FP64_UPDATE, KF_JOSEPH = 0, 1, 2
+KF_FP32, KF_FP64_UPDATE, KF_JOSEPH, KF_FP64, KF_ADAPTIVE = 0, 1, 2, 3, 4
 
 
 class KfError(RuntimeError):
@@ -47,6 +47,11 @@ class kf_layer(ctypes.Structure):
 
 
 KF_MAX_LAYERS = 64
+
+
+class kf_tuning(ctypes.Structure):
+    _fields_ = [("step_kernel", ctypes.c_int32), ("threads", ctypes.c_int32),
+                ("ctas_per_sm", ctypes.c_int32), ("ms", ctypes.c_float)]
 
 
 class kf_server_config(ctypes.Structure):
@@ -113,6 +118,17 @@ def load():
     for name in ("kf_server_create", "kf_server_submit", "kf_server_poll", "kf_server_wait",
                  "kf_server_pause", "kf_server_get_stats", "kf_server_reset_stats",
                  "kf_server_destroy"):
+        getattr(lib, name).restype = ctypes.c_int
+    lib.kf_autotune_step.argtypes = [ctypes.c_int32, ctypes.POINTER(kf_params), kf_layout] + \
+        [_VP] * 8 + [ctypes.c_int32, _VP, _VP, ctypes.POINTER(kf_tuning)]
+    lib.kf_autotune_chain.argtypes = [ctypes.POINTER(kf_params), kf_layout] + [_VP] * 5 + [
+        ctypes.POINTER(kf_layer), ctypes.c_int32, _VP, _VP, _VP, _VP, ctypes.POINTER(kf_tuning)]
+    lib.kf_autotune_export.argtypes = [ctypes.c_char_p, ctypes.c_int64,
+                                       ctypes.POINTER(ctypes.c_int64)]
+    lib.kf_autotune_import.argtypes = [ctypes.c_char_p]
+    lib.kf_autotune_clear.argtypes = []
+    for name in ("kf_autotune_step", "kf_autotune_chain", "kf_autotune_export",
+                 "kf_autotune_import", "kf_autotune_clear"):
         getattr(lib, name).restype = ctypes.c_int
     lib.kf_set_step_kernel.argtypes = [ctypes.c_int32]
     lib.kf_set_step_kernel.restype = ctypes.c_int
@@ -606,3 +622,58 @@ class Server:
 
 def kf_server_event_bytes(n: int, L: int) -> int:
     return int(load().kf_server_event_bytes(int(n), int(L)))
+
+
+# ---------------------------------------------------------------- tuning
+
+def _tuning_dict(t: kf_tuning) -> dict:
+    return {"step_kernel": {1: "direct", 2: "staged"}.get(t.step_kernel, t.step_kernel),
+            "threads": t.threads, "ctas_per_sm": t.ctas_per_sm, "ms": t.ms}
+
+
+def autotune_step(batch: "DeviceBatch", precision: int = KF_FP32) -> dict:
+    """kf_autotune_step on a resident batch (outputs to its separate arrays)."""
+    t = kf_tuning()
+    f32, i8, u8 = torch.float32, torch.int8, torch.uint8
+    kind = KF_P2Z if batch.kind == W.P2Z else KF_P2R
+    _check(load().kf_autotune_step(
+        kind, ctypes.byref(make_params(batch.bz, precision)), batch.layout,
+        _ptr(batch.state_in, "state_in", f32), _ptr(batch.cov_in, "cov_in", f32),
+        _ptr(batch.state_out, "state_out", f32), _ptr(batch.cov_out, "cov_out", f32),
+        _ptr(batch.charge, "charge", i8), _ptr(batch.hit, "hit", f32),
+        _ptr(batch.hit_cov, "hit_cov", f32), _ptr(batch.surf, "surf", f32),
+        int(batch.surf.numel() > 1), _ptr(batch.status, "status", u8), _stream(None),
+        ctypes.byref(t)))
+    return _tuning_dict(t)
+
+
+def autotune_chain(chain: "DeviceChain", precision: int = KF_FP32) -> dict:
+    """kf_autotune_chain on a resident chain workload (its state is left as it was)."""
+    t = kf_tuning()
+    f32, i8, u8 = torch.float32, torch.int8, torch.uint8
+    st_scr, cv_scr = torch.empty_like(chain.state), torch.empty_like(chain.cov)
+    _check(load().kf_autotune_chain(
+        ctypes.byref(make_params(chain.bz, precision)), chain.layout,
+        _ptr(chain.state, "state", f32), _ptr(chain.cov, "cov", f32),
+        _ptr(chain.charge, "charge", i8), _ptr(chain.hits, "hits", f32),
+        _ptr(chain.hit_covs, "hit_covs", f32), chain.layers, len(chain.layers),
+        _ptr(chain.status, "status", u8), st_scr.data_ptr(), cv_scr.data_ptr(), _stream(None),
+        ctypes.byref(t)))
+    return _tuning_dict(t)
+
+
+def autotune_export() -> str:
+    lib = load()
+    n = ctypes.c_int64(0)
+    _check(lib.kf_autotune_export(None, 0, ctypes.byref(n)))
+    buf = ctypes.create_string_buffer(n.value + 1)
+    _check(lib.kf_autotune_export(buf, n.value + 1, ctypes.byref(n)))
+    return buf.value.decode()
+
+
+def autotune_import(text: str) -> None:
+    _check(load().kf_autotune_import(text.encode()))
+
+
+def autotune_clear() -> None:
+    _check(load().kf_autotune_clear())

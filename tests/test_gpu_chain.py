@@ -14,7 +14,8 @@ from paper_2401_14221_gb300 import workload as W
 pytestmark = pytest.mark.gpu
 
 VARIANT_FORM = {kf.KF_FP32: oracle.FORM_STANDARD, kf.KF_FP64_UPDATE: oracle.FORM_STANDARD,
-                kf.KF_JOSEPH: oracle.FORM_JOSEPH}
+                kf.KF_JOSEPH: oracle.FORM_JOSEPH, kf.KF_FP64: oracle.FORM_STANDARD,
+                kf.KF_ADAPTIVE: oracle.FORM_STANDARD}
 
 
 @pytest.fixture(scope="module")
@@ -81,7 +82,8 @@ def test_chain_equals_per_layer_launches_bitwise(dev, precision):
     assert np.array_equal(fused[0], plain[0]) and np.array_equal(fused[1], plain[1])
 
 
-@pytest.mark.parametrize("precision", [kf.KF_FP32, kf.KF_FP64_UPDATE, kf.KF_JOSEPH])
+@pytest.mark.parametrize("precision", [kf.KF_FP32, kf.KF_FP64_UPDATE, kf.KF_JOSEPH, kf.KF_FP64,
+                                       kf.KF_ADAPTIVE])
 def test_chain_matches_oracle_on_256_events(dev, chain_full, precision):
     cw = chain_full
     dc = kf.chain_upload(cw, kf.KF_AOSOA, 32, dev)

@@ -23,7 +23,9 @@ pytestmark = pytest.mark.gpu
 LAYOUTS = [(kf.KF_SOA, 0), (kf.KF_AOSOA, 16), (kf.KF_AOSOA, 32), (kf.KF_AOSOA, 64),
            (kf.KF_AOSOA, 128)]
 VARIANT_FORM = {kf.KF_FP32: oracle.FORM_STANDARD, kf.KF_FP64_UPDATE: oracle.FORM_STANDARD,
-                kf.KF_JOSEPH: oracle.FORM_JOSEPH}
+                kf.KF_JOSEPH: oracle.FORM_JOSEPH, kf.KF_FP64: oracle.FORM_STANDARD,
+                kf.KF_ADAPTIVE: oracle.FORM_STANDARD}
+ALL_VARIANTS = [kf.KF_FP32, kf.KF_FP64_UPDATE, kf.KF_JOSEPH, kf.KF_FP64, kf.KF_ADAPTIVE]
 
 
 @pytest.fixture(scope="module")
@@ -107,7 +109,7 @@ def test_p2r_paper_scale_960k(dev, w_p2r, layout, step_kernel):
     assert rep["flagged"] == 0
 
 
-@pytest.mark.parametrize("precision", [kf.KF_FP32, kf.KF_FP64_UPDATE, kf.KF_JOSEPH])
+@pytest.mark.parametrize("precision", ALL_VARIANTS)
 def test_precision_study_pt_0p2_to_100(dev, w_prec, precision, step_kernel):
     for w in w_prec:
         b = run(w, dev, (kf.KF_AOSOA, 32), precision)
@@ -115,7 +117,7 @@ def test_precision_study_pt_0p2_to_100(dev, w_prec, precision, step_kernel):
 
 
 @pytest.mark.parametrize("layout", LAYOUTS[1:])
-@pytest.mark.parametrize("precision", [kf.KF_FP32, kf.KF_JOSEPH])
+@pytest.mark.parametrize("precision", [kf.KF_FP32, kf.KF_JOSEPH, kf.KF_ADAPTIVE])
 def test_staged_and_direct_kernels_agree_bitwise(dev, w_p2r, layout, precision):
     # the two kernels run the same per-track arithmetic; only the loads differ
     outs = []
@@ -162,44 +164,68 @@ def test_in_place_equals_out_of_place(dev, kind):
         assert np.array_equal(a, c)
 
 
-# 8 units of 2^-24: the rounding floor of the FP32 covariance update, relative
-# to the scale of the covariance it subtracts from (oracle/compare.py)
-EPS_FLOOR = 8 * 2.0 ** -24
-
-
-def oracle_prior_p2r(w, idx):
-    """The oracle's propagated covariance J C J^T (before the update)."""
-    out = np.empty((len(idx), 21))
-    for k, i in enumerate(idx):
-        _, J, st = oracle.propagate_to_r(w.state[:, i], int(w.charge[i]), w.bz,
-                                         float(np.broadcast_to(w.surf, (w.n,))[i]))
-        C = compare.unpack(w.cov.T[i:i + 1].astype(np.float64))[0]
-        out[k] = compare.pack((J @ C @ J.T)[None])[0]
-    return out
-
-
-def test_per_track_surfaces(dev, step_kernel):
+@pytest.mark.parametrize("precision", [kf.KF_ADAPTIVE, kf.KF_FP64])
+def test_per_track_surfaces(dev, step_kernel, precision):
     # every track has its own plane / cylinder and its hit lies on it
     rng = np.random.default_rng(8)
     zs = rng.uniform(20.0, 120.0, 3001)
     w = W.make_p2z(3001, seed=8, zt=zs)
-    b = run(w, dev, (kf.KF_SOA, 0))
+    b = run(w, dev, (kf.KF_SOA, 0), precision)
     check(w, b, np.arange(w.n))
     # Cylinders out to 150 cm: low-pT tracks reach them after long paths,
-    # some at grazing incidence, where a precise hit shrinks the propagated
-    # variance by up to ~1e6.  Covariances are compared in the surface frame
-    # with the FP32 rounding floor of the update added (see compare.py).
-    rs = rng.uniform(5.0, 150.0, 3001)  # 2 rho = 88..175 cm for pT 0.5..1 GeV: some never get there
-    w = W.make_p2r(1, 3001, seed=9, R=rs)
-    b = run(w, dev, (kf.KF_AOSOA, 32))
+    # some at grazing incidence, where the hit shrinks the propagated
+    # variance by up to ~1e6.  There the FP32 covariance update loses more
+    # digits than FP32 holds; KF_ADAPTIVE redoes those tracks in FP64.
+    # Covariances of tracks on the cylinder are compared in its surface frame.
+    # 2 rho = 88..175 cm for pT 0.5..1 GeV: some never get there
+    w = grazing_p2r()
+    b = run(w, dev, (kf.KF_AOSOA, 32), precision)
     st, cv, stat = b.download()
-    idx = np.arange(w.n)
-    o_st, o_cv, o_stat, _ = oracle_on(w, idx)
+    o_st, o_cv, o_stat, _ = oracle_on(w, np.arange(w.n))
     on_cyl = (o_stat & oracle.NO_INTERSECT) == 0
-    rep = compare.compare(st.T, cv.T, stat, o_st, o_cv, o_stat, on_cylinder=on_cyl,
-                          prior=oracle_prior_p2r(w, idx), eps_floor=EPS_FLOOR)
+    rep = compare.compare(st.T, cv.T, stat, o_st, o_cv, o_stat, on_cylinder=on_cyl)
     assert rep["ok"], rep
     assert rep["flagged"] > 0 and rep["flagged"] == int(np.sum(~w.reached))
+
+
+def grazing_p2r(seed=9, n=3001):
+    # cylinders out to 150 cm: low-pT tracks cross some at grazing incidence
+    rs = np.random.default_rng(seed).uniform(5.0, 150.0, n)
+    return W.make_p2r(1, n, seed=seed, R=rs)
+
+
+@pytest.mark.parametrize("layout", [(kf.KF_SOA, 0), (kf.KF_AOSOA, 16)])
+def test_adaptive_redo_pass_in_place(dev, step_kernel, layout):
+    # KF_ADAPTIVE marks ill-conditioned tracks in the FP32 kernel and redoes
+    # them in a second kernel from the untouched inputs; in place the FP32
+    # kernel must therefore leave those tracks' inputs alone.
+    w = grazing_p2r()
+    ref = run(w, dev, layout, kf.KF_ADAPTIVE).download()
+    fp32 = run(w, dev, layout, kf.KF_FP32).download()
+    b = kf.upload(w, layout[0], layout[1], dev)
+    b.run(kf.KF_ADAPTIVE, in_place=True)
+    torch.cuda.synchronize()
+    b.state_out, b.cov_out = b.state_in, b.cov_in
+    got = b.download()
+    for x, y in zip(ref, got):
+        assert np.array_equal(x, y)
+    # the redo pass ran: some tracks differ from FP32, and no mark is left
+    redone = np.any(ref[1] != fp32[1], axis=0) & ((ref[2] & kf.NO_INTERSECT) == 0)
+    assert 0 < int(redone.sum()) < w.n // 2
+    assert not np.any(ref[2] & 0x80)
+
+
+def test_adaptive_needs_a_status_array(dev):
+    w = W.make_p2r(1, 256, seed=5)
+    b = kf.upload(w, kf.KF_AOSOA, 32, dev)
+    b.state_out.fill_(7.0)
+    with pytest.raises(kf.KfError) as e:
+        kf.kf_p2r_propagate_update(kf.make_params(w.bz, kf.KF_ADAPTIVE), b.layout, b.state_in,
+                                   b.cov_in, b.state_out, b.cov_out, b.charge, b.hit, b.hit_cov,
+                                   b.surf, 0, None, None)
+    assert e.value.code == kf.KF_ERR_ARG
+    torch.cuda.synchronize()
+    assert torch.all(b.state_out == 7.0)
 
 
 def test_degenerate_tracks(dev, step_kernel):
