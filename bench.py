@@ -40,7 +40,9 @@ NEVTS, NTRKS, RADIUS = 100, 9600, 30.0
 # + hit cov 24 = 145, write state 24 + cov 84 = 108.
 BYTES_PER_TRACK_P2R = 253
 FALLBACK_HBM_GBS = 6800.0
+NOMINAL_HBM_GBS = 7900.0
 KERNEL_SOURCES = ("paper_2401_14221_gb300/csrc/kf_device.cuh",
+                  "paper_2401_14221_gb300/csrc/kf_step.cuh",
                   "paper_2401_14221_gb300/csrc/kf_step.cu",
                   "paper_2401_14221_gb300/csrc/kf_step_staged.cu")
 
@@ -53,7 +55,9 @@ def parse():
     ap.add_argument("--impl", choices=["kf", "reference"], default="kf")
     ap.add_argument("--layout", default="auto",
                     help="auto | soa | aosoa16 | aosoa32 | aosoa64 | aosoa128")
-    ap.add_argument("--step-kernel", default="auto", choices=["auto", "direct", "staged"])
+    ap.add_argument("--step-kernel", default="auto",
+                    choices=["auto", "direct", "staged", "staged2", "staged3"],
+                    help="staged = staged2: 2 CTAs/SM x 3 stages; staged3: 3 CTAs/SM x 2 stages")
     ap.add_argument("--e2e-steps", type=int, default=30)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-chain", action="store_true",
@@ -67,7 +71,7 @@ def parse():
                     help="Poisson arrival rates of the serving measurement, events/s")
     ap.add_argument("--profile-only", action="store_true",
                     help="run a few launches of one layout and exit (for ncu captures)")
-    ap.add_argument("--kind", choices=["p2r", "p2z"], default="p2r",
+    ap.add_argument("--kind", choices=["p2r", "p2z", "chain"], default="p2r",
                     help="workload of --profile-only")
     ap.add_argument("--e2e-chunk", type=int, default=0,
                     help="tracks per pipeline chunk of the host-array call (0 = library default)")
@@ -226,9 +230,19 @@ def cpu_baseline(w):
         el = time.perf_counter() - t0
         if el > 2.0 or passes >= 20 or (time.process_time() - c0) > 20.0:
             break
+    cpu_s = time.process_time() - c0
+    # one core: a slice of the same workload
+    m = min(w.n, 60000)
+    sl = (slice(0, m), slice(None))
+    t1 = time.perf_counter()
+    oracle.step_batch(W.P2R, state[sl], cov[sl], w.charge[:m], hit[sl], hc[sl], w.surf, w.bz,
+                      threads=1)
+    one = m / (time.perf_counter() - t1)
     return {"value": passes * w.n / el, "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": f"{passes} full pass(es) over the {w.n}-track workload, "
-                      f"{time.process_time() - c0:.1f} s CPU time"}
+                      f"{cpu_s:.1f} s CPU time",
+            "single_core_value": one,
+            "single_core_sample": f"the first {m} tracks of the workload on one thread"}
 
 
 def compressed_bench(kf, W, w, dev, kind, width):
@@ -277,20 +291,27 @@ def chain_bench(args, kf, W, dev, rank):
     cw = W.make_chain(events=256, seed=shard.rank_seed(7, rank))
     dc = kf.chain_upload(cw, kf.KF_AOSOA, 32, dev)
     L = cw.L
-    # per-layer launches captured once in a CUDA graph
+    # the library's chain autotuner picks the CTA size (served from its cache)
+    tuned = kf.autotune_chain(dc)
     stream = torch.cuda.Stream()
-    plain_graph = None
-    try:
-        dc.reset()
-        with torch.cuda.stream(stream):
-            dc.run_plain(stream=stream)
-        torch.cuda.synchronize()
-        plain_graph = torch.cuda.CUDAGraph()
-        with torch.cuda.graph(plain_graph, stream=stream):
-            dc.run_plain()
-        torch.cuda.synchronize()
-    except Exception:
-        plain_graph = None
+
+    def capture(fn):
+        # one fused launch, or the L per-layer launches, captured in a CUDA graph
+        try:
+            dc.reset()
+            with torch.cuda.stream(stream):
+                fn(stream=stream)
+            torch.cuda.synchronize()
+            g = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(g, stream=stream):
+                fn()
+            torch.cuda.synchronize()
+            return g
+        except Exception:
+            return None
+
+    fused_graph = capture(dc.run)
+    plain_graph = capture(dc.run_plain)
 
     def timed(fn, reps):
         ms = []
@@ -306,8 +327,9 @@ def chain_bench(args, kf, W, dev, rank):
         return sorted(ms)[len(ms) // 2]
 
     reps = max(3, args.chain_steps)
-    timed(dc.run, 2)
-    fused_ms = timed(dc.run, reps)
+    fused_fn = fused_graph.replay if fused_graph is not None else dc.run
+    timed(fused_fn, 2)
+    fused_ms = timed(fused_fn, reps)
     plain_fn = plain_graph.replay if plain_graph is not None else dc.run_plain
     timed(plain_fn, 2)
     plain_ms = timed(plain_fn, reps)
@@ -325,7 +347,9 @@ def chain_bench(args, kf, W, dev, rank):
             "fused_GBps": fused_b * cw.n / (fused_ms * 1e-3) / 1e9,
             "plain_GBps": plain_b * cw.n / (plain_ms * 1e-3) / 1e9,
             "bytes_per_track": {"fused": fused_b, "plain": plain_b},
+            "fused_launch": "CUDA graph" if fused_graph is not None else "eager",
             "plain_launch": "CUDA graph" if plain_graph is not None else "eager",
+            "autotune": tuned,
             "timing": f"median of {reps} runs, CUDA events, state reset outside the timed pair"}
 
 
@@ -474,12 +498,23 @@ def main():
     layouts = {"soa": (kf.KF_SOA, 0), "aosoa16": (kf.KF_AOSOA, 16), "aosoa32": (kf.KF_AOSOA, 32),
                "aosoa64": (kf.KF_AOSOA, 64), "aosoa128": (kf.KF_AOSOA, 128)}
 
+    if args.profile_only and args.kind == "chain":
+        # the fused chain on 64 events of the chain workload, a few launches
+        cw = W.make_chain(events=64, seed=7)
+        dc = kf.chain_upload(cw, kf.KF_AOSOA, 32, dev)
+        for _ in range(3):
+            dc.run()
+        torch.cuda.synchronize()
+        print(f"profile-only: chain n={cw.n} L={cw.L}: 3 launches done")
+        return 0
     if args.profile_only:
         w = (W.make_p2r(NEVTS, NTRKS, seed=1) if args.kind == "p2r"
              else W.make_p2z(NEVTS * NTRKS, seed=1))
         kind, width = layouts["aosoa16" if args.layout == "auto" else args.layout]
         kf.kf_set_step_kernel({"auto": kf.KF_STEP_AUTO, "direct": kf.KF_STEP_DIRECT,
-                               "staged": kf.KF_STEP_STAGED}[args.step_kernel])
+                               "staged": kf.KF_STEP_STAGED, "staged2": kf.KF_STEP_STAGED,
+                               "staged3": kf.KF_STEP_STAGED}[args.step_kernel])
+        kf.kf_set_staged_ctas_per_sm(3 if args.step_kernel == "staged3" else 2)
         bs = [kf.upload(w, kind, width, dev) for _ in range(2)]
         for i in range(5):
             bs[i % 2].run()
@@ -501,7 +536,8 @@ def main():
 
     # Kernel x layout sweep (outside the timed region): the direct kernel on
     # SoA and AoSoA, the staged kernel on AoSoA block widths.
-    modes = {"direct": kf.KF_STEP_DIRECT, "staged": kf.KF_STEP_STAGED}
+    modes = {"direct": kf.KF_STEP_DIRECT, "staged": kf.KF_STEP_STAGED,
+             "staged2": kf.KF_STEP_STAGED, "staged3": kf.KF_STEP_STAGED}
     sweep = {}
     if args.layout == "auto" or args.step_kernel == "auto":
         for lname, (kind, width) in layouts.items():
@@ -509,11 +545,13 @@ def main():
                 continue
             bs = [kf.upload(w, kind, width, dev) for _ in range(2)]
             for mname, mode in modes.items():
-                if kind == kf.KF_SOA and mname == "staged":
+                if kind == kf.KF_SOA and mname.startswith("staged"):
                     continue
                 if args.step_kernel != "auto" and mname != args.step_kernel:
                     continue
                 kf.kf_set_step_kernel(mode)
+                # staged: 2 CTAs per SM x 3 stages; staged3: 3 x 2 stages
+                kf.kf_set_staged_ctas_per_sm(3 if mname == "staged3" else 2)
                 time_launches(bs, 20)
                 ms = time_launches(bs, 200)
                 sweep[f"{mname}/{lname}"] = {"ms": ms, "tracks_per_s": w.n / (ms * 1e-3)}
@@ -523,6 +561,7 @@ def main():
     else:
         chosen_kernel, chosen = args.step_kernel, args.layout
     kf.kf_set_step_kernel(modes[chosen_kernel])
+    kf.kf_set_staged_ctas_per_sm(3 if chosen_kernel == "staged3" else 2)
     kind, width = layouts[chosen]
     sets = [kf.upload(w, kind, width, dev) for _ in range(4)]
     tuned = None
@@ -582,6 +621,22 @@ def main():
     ms_per_step = elapsed_ms / args.steps
     value = shard.whole_job_throughput(w.n, args.steps, world, elapsed_ms * 1e-3)
 
+    # Spread: ten timed repeats of a tenth of the steps each.
+    reps = []
+    kr = max(args.steps // 10, 4)
+    for _ in range(10):
+        r0, r1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        r0.record()
+        run_steps(kr)
+        r1.record()
+        torch.cuda.synchronize()
+        reps.append(r0.elapsed_time(r1) / kr)
+    reps_sorted = sorted(reps)
+    spread = {"repeats": 10, "steps_each": kr,
+              "ms_per_step_mean": sum(reps) / 10,
+              "ms_per_step_sd": (sum((x - sum(reps) / 10) ** 2 for x in reps) / 9) ** 0.5,
+              "ms_per_step_p50": 0.5 * (reps_sorted[4] + reps_sorted[5])}
+
     # Roofline of the step kernel: algorithmic bytes / average launch time.
     peak, peak_src = measured_hbm_peak()
     achieved = BYTES_PER_TRACK_P2R * w.n / (ms_per_step * 1e-3) / 1e9
@@ -605,6 +660,17 @@ def main():
            "h2d_bytes_per_step": hb.h2d_bytes(), "d2h_bytes_per_step": hb.d2h_bytes(),
            "ms_per_step": e2e_ms, "host_memory": "pinned"}
     del hb
+    # the same from pageable host memory (context: the driver stages it)
+    hp = kf.host_upload(w, kind, width, dev, chunk_tracks=args.e2e_chunk, pinned=False)
+    hp.run()
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(ke):
+        hp.run()
+    e1.record()
+    torch.cuda.synchronize()
+    e2e["pageable_value"] = w.n / (e0.elapsed_time(e1) / ke * 1e-3)
+    del hp
 
     # Update variants and the compressed covariance store on the same batch
     # (context for the precision study; errors are measured by the tests).
@@ -654,6 +720,7 @@ def main():
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic,
                          "peak_source": peak_src,
+                         "frac_of_nominal_7900": achieved / NOMINAL_HBM_GBS,
                          "bytes_per_track": BYTES_PER_TRACK_P2R},
             "variants": variants,
             "chain": chain,
@@ -662,6 +729,7 @@ def main():
             "e2e": e2e,
             "gpu_launches": args.steps,
             "clocks": clocks,
+            "spread": spread,
             "sweep": sweep,
             "autotune": tuned,
             "device_error": kf.kf_take_device_error(),

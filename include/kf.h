@@ -328,13 +328,15 @@ int kf_propagate_update_host_noalloc(int32_t kind, const kf_params *params,
  * n bucket = floor(log2 n)); later calls in KF_STEP_AUTO mode use it.  No
  * paper counterpart (the paper fixes bsize and launch shapes by hand).
  * Single-step candidates: one thread per track with 128 or 256 threads per
- * CTA; for AoSoA also the persistent staged kernel with 1 or 2 CTAs per SM.
+ * CTA; for AoSoA also the persistent staged kernel with 1, 2 or 3 CTAs per
+ * SM (3: two pipeline stages per CTA instead of three, FP32-arithmetic
+ * variants only; the others run it as 2).
  * Chain candidates: 64, 128 or 256 threads per CTA.
  */
 typedef struct {
     int32_t step_kernel;  /* KF_STEP_DIRECT or KF_STEP_STAGED               */
     int32_t threads;      /* threads per CTA (one-thread-per-track kernels) */
-    int32_t ctas_per_sm;  /* persistent CTAs per SM (staged kernel)         */
+    int32_t ctas_per_sm;  /* persistent CTAs per SM (staged kernel), 1-3    */
     float   ms;           /* measured time per call of the chosen shape     */
 } kf_tuning;
 
@@ -462,6 +464,16 @@ int kf_server_destroy(kf_server *s);
 #define KF_STEP_DIRECT 1
 #define KF_STEP_STAGED 2
 int kf_set_step_kernel(int32_t mode);
+
+/*
+ * kf_set_staged_ctas_per_sm -- resident CTAs per SM of the staged kernel
+ * under KF_STEP_STAGED (the autotuner's choice applies under KF_STEP_AUTO):
+ * 1 or 2 (three pipeline stages per CTA), 3 (two stages per CTA, more
+ * compute warps per SM; FP32-arithmetic variants, the others run 2), or 0
+ * for the default 2.  Results are the same, bit for bit.  Returns
+ * KF_ERR_ARG outside 0..3.
+ */
+int kf_set_staged_ctas_per_sm(int32_t ctas);
 
 /*
  * kf_take_device_error -- read and clear the library's device error word

@@ -259,8 +259,8 @@ __device__ __forceinline__ bool propagate_to_z(const T (&in)[6], T qf, T bz, T z
 // ------------------------------------------------------------------- p2r
 // Propagate to the first outward crossing of the cylinder r = R.  Returns
 // false when the track starts on/outside the cylinder or never reaches it.
-// cos_inc receives the cosine between the track direction and the surface
-// normal at the crossing.
+// rcos receives R times the cosine between the track direction and the
+// surface normal at the crossing (the incidence test needs no division).
 //
 // With A = P0.t0, B = P0.n0 (t0 = (cos phi, sin phi), n0 = (-sin, cos)),
 // d = R^2 - |P0|^2 and t = tan(h), the crossing condition becomes
@@ -269,7 +269,7 @@ __device__ __forceinline__ bool propagate_to_z(const T (&in)[6], T qf, T bz, T z
 //   (cos h, sin h) = (2 (A + sqrt(.)), omega d) / norm,  chord = 2 d / norm.
 template <class T>
 __device__ __forceinline__ bool propagate_to_r(const T (&in)[6], T qf, T bz, T R, T (&out)[6],
-                                               T (&J)[36], T &cos_inc) {
+                                               T (&J)[36], T &rcos) {
   using F = Fp<T>;
   const T x = in[0], y = in[1], z = in[2], k = in[3], phi = in[4], th = in[5];
   const T r0sq = F::fma_(x, x, y * y);
@@ -319,7 +319,7 @@ __device__ __forceinline__ bool propagate_to_r(const T (&in)[6], T qf, T bz, T R
   const T Yphi = L * cpm;
   // s(p) from g = x'^2 + y'^2 - R^2 = 0: ds/dp = -(x' dx'/dp + y' dy'/dp) / (x' cos + y' sin).
   const T gs = F::fma_(x1, cp1, y1 * sp1);
-  cos_inc = gs / R;
+  rcos = gs;
   const T ig = T(-1) / gs;
   const T dsx = ig * x1;
   const T dsy = ig * y1;
@@ -522,12 +522,12 @@ __device__ __forceinline__ unsigned p2z_step_t(T (&p)[6], T (&C)[21], T qf, T bz
 template <class T, int FORM>
 __device__ __forceinline__ unsigned p2r_step_t(T (&p)[6], T (&C)[21], T qf, T bz, T R, T hx,
                                                T hy, T hz, const T (&hc)[6], T &shrink,
-                                               T &cos_inc) {
+                                               T &rcos) {
   using F = Fp<T>;
   T pp[6], J[36], Cp[21];
   shrink = T(0);
-  cos_inc = T(1);
-  if (!propagate_to_r(p, qf, bz, R, pp, J, cos_inc)) return kNoIntersect;
+  rcos = R;
+  if (!propagate_to_r(p, qf, bz, R, pp, J, rcos)) return kNoIntersect;
   const T ip = F::rsqrt_(F::fma_(pp[0], pp[0], pp[1] * pp[1]));
   const T ca = pp[0] * ip, sa = pp[1] * ip;  // direction of P'
 #pragma unroll
@@ -632,14 +632,15 @@ __device__ __forceinline__ unsigned step_variant(float (&p)[6], float (&C)[21], 
   } else {
     constexpr int FORM = VARIANT == kJoseph ? kJosephForm
                          : VARIANT == kFP64Update ? kStandardF64 : kStandard;
-    float ill, cinc = 1.0f;
+    float ill, rcos = surf;
     unsigned st;
     if (KIND == kP2z)
       st = p2z_step_t<float, FORM>(p, C, qf, bz, surf, hx, hy, hc[0], hc[1], hc[2], ill);
     else
-      st = p2r_step_t<float, FORM>(p, C, qf, bz, surf, hx, hy, hz, hc, ill, cinc);
+      st = p2r_step_t<float, FORM>(p, C, qf, bz, surf, hx, hy, hz, hc, ill, rcos);
     if constexpr (VARIANT == kAdaptive) {
-      if (!(st & kNoIntersect) && (ill != 0.0f || !(fabsf(cinc) >= kRedoGrazing))) st |= kRedo;
+      if (!(st & kNoIntersect) && (ill != 0.0f || !(fabsf(rcos) >= kRedoGrazing * surf)))
+        st |= kRedo;
     }
     return st;
   }

@@ -79,19 +79,39 @@ __global__ void __launch_bounds__(256) step_kernel(const __grid_constant__ StepA
   if (a.status) a.status[i] = (uint8_t)st;
 }
 
-// The redo pass of KF_ADAPTIVE: a grid-stride scan of the status bytes (a
-// warp reads 32 consecutive bytes); marked tracks run the FP64 step.
+// The redo pass of KF_ADAPTIVE.  Each thread checks 16 consecutive status
+// bytes with one 16-byte load (byte loads where the array is not 16-byte
+// aligned or at the ragged end), so the scan costs one load per thread in a
+// single wave; only marked tracks run the FP64 step.
+constexpr int kRedoScan = 16;
+
 template <int KIND>
 __global__ void __launch_bounds__(256) redo_pass_kernel(const __grid_constant__ StepArgs a) {
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += stride)
-    if (a.status[i] & kRedo) a.status[i] = (uint8_t)redo_track_fp64<KIND>(a, i);
+  const int64_t base = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * kRedoScan;
+  if (base >= a.n) return;
+  uint8_t m[kRedoScan];
+  if (base + kRedoScan <= a.n && (reinterpret_cast<uintptr_t>(a.status) & 15u) == 0) {
+    const uint4 v = *reinterpret_cast<const uint4 *>(a.status + base);
+    const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+    for (int j = 0; j < kRedoScan; ++j) m[j] = (uint8_t)(w[j >> 2] >> (8 * (j & 3)));
+  } else {
+#pragma unroll
+    for (int j = 0; j < kRedoScan; ++j) m[j] = base + j < a.n ? a.status[base + j] : 0;
+  }
+  unsigned any = 0;
+#pragma unroll
+  for (int j = 0; j < kRedoScan; ++j) any |= m[j];
+  if (!(any & kRedo)) return;
+  for (int j = 0; j < kRedoScan; ++j)
+    if (m[j] & kRedo) a.status[base + j] = (uint8_t)redo_track_fp64<KIND>(a, base + j);
 }
 
 int launch_redo_pass(int kind, const StepArgs &a, cudaStream_t s) {
   if (a.n == 0) return KF_OK;
-  const int64_t blocks = (a.n + 255) / 256;
-  const unsigned g = (unsigned)(blocks < 1024 ? blocks : 1024);
+  const int64_t blocks = (a.n + 256 * kRedoScan - 1) / (256 * kRedoScan);
+  if (blocks > 0x7fffffffLL) return set_error(KF_ERR_ARG, "n too large for one launch");
+  const unsigned g = (unsigned)blocks;
   if (kind == kP2z)
     redo_pass_kernel<kP2z><<<g, 256, 0, s>>>(a);
   else
@@ -145,6 +165,7 @@ static int launch_step(const kf_params *params, kf_layout layout, const float *s
 
 namespace {
 std::atomic<int> g_step_mode{KF_STEP_AUTO};
+std::atomic<int> g_staged_ctas{0};
 }
 
 int step_kernel_mode() { return g_step_mode.load(std::memory_order_relaxed); }
@@ -167,6 +188,9 @@ static int launch_step_main(int kind, int precision, const StepArgs &a, cudaStre
     const int mode = step_kernel_mode();
     if (mode == KF_STEP_DIRECT) {
       cfg.kernel = KF_STEP_DIRECT;
+    } else if (mode == KF_STEP_STAGED) {
+      const int c = g_staged_ctas.load(std::memory_order_relaxed);
+      if (c > 0) cfg.ctas_per_sm = c;
     } else if (mode == KF_STEP_AUTO) {
       LaunchConfig t;
       if (tune_lookup(kOpStep, kind, precision, a.soa, a.lw, a.n, &t)) cfg = t;
@@ -226,5 +250,12 @@ extern "C" int kf_set_step_kernel(int32_t mode) {
   if (mode != KF_STEP_AUTO && mode != KF_STEP_DIRECT && mode != KF_STEP_STAGED)
     return kf::set_error(KF_ERR_ARG, "unknown step kernel mode %d", mode);
   kf::g_step_mode.store(mode, std::memory_order_relaxed);
+  return KF_OK;
+}
+
+extern "C" int kf_set_staged_ctas_per_sm(int32_t ctas) {
+  kf::clear_error();
+  if (ctas < 0 || ctas > 3) return kf::set_error(KF_ERR_ARG, "ctas_per_sm = %d is not 0..3", ctas);
+  kf::g_staged_ctas.store(ctas, std::memory_order_relaxed);
   return KF_OK;
 }

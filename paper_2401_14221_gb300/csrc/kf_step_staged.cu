@@ -36,13 +36,16 @@ namespace staged {
 constexpr int kComputeWarps = 8;
 constexpr int kThreads = (kComputeWarps + 1) * 32;
 constexpr int kT = kComputeWarps * 32;  // tracks per tile
-constexpr int kStages = 3;
 constexpr int kStateB = kT * 6 * 4;
 constexpr int kCovB = kT * 21 * 4;
 constexpr int kHitB = kT * 3 * 4;
 constexpr int kHcB = kT * 6 * 4;
 constexpr int kStageB = kStateB + kCovB + kHitB + kHcB;
-constexpr int kSmemBytes = kStages * kStageB + 2 * kStages * 8;
+// Pipeline depth per CTA for a given number of resident CTAs per SM: the
+// SM's shared memory holds six stages, as 3 stages x 2 CTAs or 2 x 3 (the
+// latter with more compute warps per SM, at <= 72 registers a thread).
+constexpr int stages_for(int ctas) { return ctas >= 3 ? 2 : 3; }
+constexpr int smem_bytes(int ctas) { return stages_for(ctas) * (kStageB + 16); }
 // Polls of a barrier before giving up (with back-off, several seconds).
 constexpr uint32_t kMaxPolls = 1u << 24;
 
@@ -112,21 +115,64 @@ __device__ __forceinline__ void bulk_g2s(void *sdst, const void *gsrc, uint32_t 
       : "memory");
 }
 
-template <int KIND, int VARIANT, int W>
-__global__ void __launch_bounds__(kThreads, 2) step_staged_kernel(const __grid_constant__ StepArgs a) {
+// Tile schedule of the persistent grid (G CTAs).  Full tiles of kT tracks go
+// round-robin (tile k of CTA b is global tile k G + b), so at any moment the
+// grid works on one narrow window of the arrays.  What is left after the
+// last complete round (fewer than G + 1 tiles' worth) is cut into G equal
+// pieces of whole AoSoA blocks, at most kT tracks each, so that the final
+// round keeps every CTA busy instead of a third of them.
+struct Schedule {
+  int64_t R;     // complete rounds of full tiles
+  int64_t base;  // first track of the remainder
+  int64_t per;   // tracks per remainder piece (multiple of W, <= kT)
+  int64_t P;     // remainder pieces
+  int64_t G;
+
+  __device__ __forceinline__ int64_t tiles_of(int64_t b) const {
+    return R + (b < P ? (P - 1 - b) / G + 1 : 0);
+  }
+  __device__ __forceinline__ void tile(int64_t k, int64_t b, int64_t n, int64_t *first,
+                                       int64_t *m) const {
+    if (k < R) {
+      *first = (k * G + b) * kT;
+      *m = kT;
+    } else {
+      *first = base + (b + (k - R) * G) * per;
+      *m = (n - *first < per) ? n - *first : per;
+    }
+  }
+};
+
+template <int W>
+__device__ __forceinline__ Schedule make_schedule(int64_t n, int64_t G) {
+  Schedule s;
+  s.G = G;
+  s.R = (n / kT) / G;
+  s.base = s.R * G * kT;
+  const int64_t rem = n - s.base;
+  if (rem == 0) {
+    s.per = kT;
+    s.P = 0;
+  } else {
+    const int64_t share = ((rem + G - 1) / G + W - 1) / W * W;
+    s.per = share < kT ? share : kT;
+    s.P = (rem + s.per - 1) / s.per;
+  }
+  return s;
+}
+
+template <int KIND, int VARIANT, int W, int CTAS>
+__global__ void __launch_bounds__(kThreads, CTAS)
+    step_staged_kernel(const __grid_constant__ StepArgs a) {
   static_assert(kT % W == 0, "tile must hold whole AoSoA blocks");
+  constexpr int kStages = stages_for(CTAS);
   extern __shared__ __align__(128) unsigned char smem[];
   uint64_t *full = reinterpret_cast<uint64_t *>(smem + kStages * kStageB);
   uint64_t *empty = full + kStages;
   const int warp = threadIdx.x >> 5;
   const int lane = threadIdx.x & 31;
-  // Balanced contiguous ranges: CTA b owns tracks [begin, end), the same
-  // number of whole AoSoA blocks for every CTA, processed in tiles of kT
-  // (the last one partial), so all CTAs finish within one block of each other.
-  const int64_t per = (((a.n + gridDim.x - 1) / gridDim.x) + W - 1) / W * W;
-  const int64_t begin = (int64_t)blockIdx.x * per;
-  const int64_t end = (begin + per < a.n) ? begin + per : a.n;
-  const int64_t ntiles = (begin < end) ? (end - begin + kT - 1) / kT : 0;
+  const Schedule sch = make_schedule<W>(a.n, gridDim.x);
+  const int64_t ntiles = sch.tiles_of(blockIdx.x);
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < kStages; ++s) {
@@ -144,8 +190,8 @@ __global__ void __launch_bounds__(kThreads, 2) step_staged_kernel(const __grid_c
         const int s = (int)(k % kStages);
         const uint32_t ph = (uint32_t)(k / kStages) & 1u;
         if (k >= kStages && !mbar_wait(&empty[s], ph ^ 1u)) break;
-        const int64_t first = begin + k * kT;
-        const int64_t m = (end - first < kT) ? end - first : kT;
+        int64_t first, m;
+        sch.tile(k, blockIdx.x, a.n, &first, &m);
         const uint32_t cols = (uint32_t)(((m + W - 1) / W) * W);  // whole blocks
         unsigned char *st = smem + s * kStageB;
         mbar_arrive_expect_tx(&full[s], cols * (6 + 21 + 3 + 6) * 4);
@@ -161,14 +207,27 @@ __global__ void __launch_bounds__(kThreads, 2) step_staged_kernel(const __grid_c
   // --------------------------------------------------------------- compute
   const int il = warp * 32 + lane;          // track within the tile
   const int blk = il / W, r = il % W;       // AoSoA block and slot within the tile
+  // charge and the per-track surface are plain [n] arrays, read directly;
+  // each tile's values are requested one tile ahead so that their latency
+  // hides behind the previous tile's step.
+  auto fetch = [&](int64_t k, float &q, float &sf) {
+    int64_t f, mm;
+    sch.tile(k, blockIdx.x, a.n, &f, &mm);
+    const bool lv = il < mm;
+    q = lv ? (float)__ldg(a.charge + f + il) : 1.0f;
+    sf = __ldg(a.surf + ((a.surf_per_track && lv) ? f + il : 0));
+  };
+  float qf_next = 1.0f, surf_next = 0.0f;
+  if (ntiles > 0) fetch(0, qf_next, surf_next);
   for (int64_t k = 0; k < ntiles; ++k) {
     const int s = (int)(k % kStages);
     const uint32_t ph = (uint32_t)(k / kStages) & 1u;
-    const int64_t i = begin + k * kT + il;
-    const bool live = i < end;
-    // plain per-track arrays: issue before waiting on the stage
-    const float qf = live ? (float)__ldg(a.charge + i) : 1.0f;
-    const float surf = __ldg(a.surf + ((a.surf_per_track && live) ? i : 0));
+    int64_t first, m;
+    sch.tile(k, blockIdx.x, a.n, &first, &m);
+    const int64_t i = first + il;
+    const bool live = il < m;
+    const float qf = qf_next, surf = surf_next;
+    if (k + 1 < ntiles) fetch(k + 1, qf_next, surf_next);
     if (!mbar_wait(&full[s], ph)) break;
 
     const float *sst = reinterpret_cast<const float *>(smem + s * kStageB);
@@ -219,29 +278,40 @@ __global__ void __launch_bounds__(kThreads, 2) step_staged_kernel(const __grid_c
   }
 }
 
-template <int KIND, int VARIANT, int W>
+template <int KIND, int VARIANT, int W, int CTAS>
 int launch_w(const StepArgs &a, cudaStream_t s, int grid, int dev) {
-  auto kern = step_staged_kernel<KIND, VARIANT, W>;
+  auto kern = step_staged_kernel<KIND, VARIANT, W, CTAS>;
+  constexpr int smem = smem_bytes(CTAS);
   static bool configured[64] = {};  // per instantiation and device
   if (dev < 0 || dev >= 64 || !configured[dev]) {
     if (int rc = check_cuda(
-            cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes),
+            cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem),
             "cudaFuncSetAttribute"))
       return rc;
     if (dev >= 0 && dev < 64) configured[dev] = true;
   }
-  kern<<<grid, kThreads, kSmemBytes, s>>>(a);
+  kern<<<grid, kThreads, smem, s>>>(a);
   return check_cuda(cudaGetLastError(), "staged step launch");
 }
 
-template <int KIND, int VARIANT>
-int launch_v(const StepArgs &a, cudaStream_t s, int grid, int dev) {
+template <int KIND, int VARIANT, int CTAS>
+int launch_c(const StepArgs &a, cudaStream_t s, int grid, int dev) {
   switch (a.lw) {
-    case 4: return launch_w<KIND, VARIANT, 16>(a, s, grid, dev);
-    case 5: return launch_w<KIND, VARIANT, 32>(a, s, grid, dev);
-    case 6: return launch_w<KIND, VARIANT, 64>(a, s, grid, dev);
-    default: return launch_w<KIND, VARIANT, 128>(a, s, grid, dev);
+    case 4: return launch_w<KIND, VARIANT, 16, CTAS>(a, s, grid, dev);
+    case 5: return launch_w<KIND, VARIANT, 32, CTAS>(a, s, grid, dev);
+    case 6: return launch_w<KIND, VARIANT, 64, CTAS>(a, s, grid, dev);
+    default: return launch_w<KIND, VARIANT, 128, CTAS>(a, s, grid, dev);
   }
+}
+
+// Three CTAs per SM exist for the FP32-arithmetic variants (the FP64 ones
+// need more than 72 registers a thread); others take the two-CTA shape.
+template <int KIND, int VARIANT>
+int launch_v(const StepArgs &a, cudaStream_t s, int grid, int dev, int ctas) {
+  if constexpr (VARIANT == kFP32 || VARIANT == kAdaptive || VARIANT == kJoseph) {
+    if (ctas == 3) return launch_c<KIND, VARIANT, 3>(a, s, grid, dev);
+  }
+  return launch_c<KIND, VARIANT, 2>(a, s, grid, dev);
 }
 
 std::mutex g_sm_mu;
@@ -264,8 +334,8 @@ int sm_count(int dev, int *out) {
 
 }  // namespace staged
 
-// Persistent staged launch for AoSoA layouts: one or two CTAs per SM, each
-// working through its own contiguous, equal share of whole AoSoA blocks.
+// Persistent staged launch for AoSoA layouts: one or two CTAs per SM,
+// tiles scheduled as in Schedule.
 int launch_step_staged(int kind, int precision, const StepArgs &a, cudaStream_t s,
                        int ctas_per_sm) {
   using namespace staged;
@@ -275,23 +345,26 @@ int launch_step_staged(int kind, int precision, const StepArgs &a, cudaStream_t 
   if (int rc = check_cuda(cudaGetDevice(&dev), "cudaGetDevice")) return rc;
   if (int rc = sm_count(dev, &sms)) return rc;
   const int64_t ntiles = (a.n + kT - 1) / kT;
-  const int64_t slots = (int64_t)sms * (ctas_per_sm == 1 ? 1 : 2);
+  const int ctas = (ctas_per_sm == 1 || ctas_per_sm == 3) ? ctas_per_sm : 2;
+  const bool three = ctas == 3 && (precision == KF_FP32 || precision == KF_ADAPTIVE ||
+                                   precision == KF_JOSEPH);
+  const int64_t slots = (int64_t)sms * (three ? 3 : (ctas == 1 ? 1 : 2));
   const int grid = (int)(ntiles < slots ? ntiles : slots);
   if (kind == kP2z) {
     switch (precision) {
-      case KF_FP32: return launch_v<kP2z, kFP32>(a, s, grid, dev);
-      case KF_FP64_UPDATE: return launch_v<kP2z, kFP64Update>(a, s, grid, dev);
-      case KF_JOSEPH: return launch_v<kP2z, kJoseph>(a, s, grid, dev);
-      case KF_FP64: return launch_v<kP2z, kFP64>(a, s, grid, dev);
-      default: return launch_v<kP2z, kAdaptive>(a, s, grid, dev);
+      case KF_FP32: return launch_v<kP2z, kFP32>(a, s, grid, dev, ctas);
+      case KF_FP64_UPDATE: return launch_v<kP2z, kFP64Update>(a, s, grid, dev, ctas);
+      case KF_JOSEPH: return launch_v<kP2z, kJoseph>(a, s, grid, dev, ctas);
+      case KF_FP64: return launch_v<kP2z, kFP64>(a, s, grid, dev, ctas);
+      default: return launch_v<kP2z, kAdaptive>(a, s, grid, dev, ctas);
     }
   }
   switch (precision) {
-    case KF_FP32: return launch_v<kP2r, kFP32>(a, s, grid, dev);
-    case KF_FP64_UPDATE: return launch_v<kP2r, kFP64Update>(a, s, grid, dev);
-    case KF_JOSEPH: return launch_v<kP2r, kJoseph>(a, s, grid, dev);
-    case KF_FP64: return launch_v<kP2r, kFP64>(a, s, grid, dev);
-    default: return launch_v<kP2r, kAdaptive>(a, s, grid, dev);
+    case KF_FP32: return launch_v<kP2r, kFP32>(a, s, grid, dev, ctas);
+    case KF_FP64_UPDATE: return launch_v<kP2r, kFP64Update>(a, s, grid, dev, ctas);
+    case KF_JOSEPH: return launch_v<kP2r, kJoseph>(a, s, grid, dev, ctas);
+    case KF_FP64: return launch_v<kP2r, kFP64>(a, s, grid, dev, ctas);
+    default: return launch_v<kP2r, kAdaptive>(a, s, grid, dev, ctas);
   }
 }
 

@@ -130,11 +130,12 @@ extern "C" int kf_autotune_step(int32_t kind, const kf_params *params, kf_layout
                                          charge, hit, hit_cov, surf, surf_per_track, status,
                                          stream);
   };
-  LaunchConfig cands[4] = {{KF_STEP_DIRECT, 128, 0},
+  LaunchConfig cands[5] = {{KF_STEP_DIRECT, 128, 0},
                            {KF_STEP_DIRECT, 256, 0},
                            {KF_STEP_STAGED, 256, 1},
-                           {KF_STEP_STAGED, 256, 2}};
-  const int ncand = d.soa ? 2 : 4;
+                           {KF_STEP_STAGED, 256, 2},
+                           {KF_STEP_STAGED, 256, 3}};
+  const int ncand = d.soa ? 2 : 5;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   int best = -1;
   float best_ms = 0.0f;
@@ -276,6 +277,11 @@ extern "C" int kf_autotune_import(const char *text) {
     if (sscanf(line.c_str() + bar + 1, "%d|%d|%d|%d|%d|%d|%d|%d|%d|%g", &op, &kind, &prec, &soa,
                &lw, &nb, &kern, &thr, &cps, &ms) != 10)
       return set_error(KF_ERR_ARG, "line %d: malformed entry", lineno);
+    if ((op != kOpStep && op != kOpChain) || (kind != KF_P2Z && kind != KF_P2R) ||
+        prec < KF_FP32 || prec > KF_ADAPTIVE || (soa != 0 && soa != 1) || lw < 0 || lw > 7 ||
+        (kern != KF_STEP_DIRECT && kern != KF_STEP_STAGED) ||
+        (thr != 64 && thr != 128 && thr != 256) || cps < 0 || cps > 3 || !(ms >= 0.0f))
+      return set_error(KF_ERR_ARG, "line %d: value out of range", lineno);
     g_tune[Key(line.substr(0, bar), op, kind, prec, soa, lw, nb)] =
         Entry{LaunchConfig{kern, thr, cps}, ms};
   }

@@ -132,6 +132,8 @@ def load():
         getattr(lib, name).restype = ctypes.c_int
     lib.kf_set_step_kernel.argtypes = [ctypes.c_int32]
     lib.kf_set_step_kernel.restype = ctypes.c_int
+    lib.kf_set_staged_ctas_per_sm.argtypes = [ctypes.c_int32]
+    lib.kf_set_staged_ctas_per_sm.restype = ctypes.c_int
     lib.kf_take_device_error.argtypes = [ctypes.POINTER(ctypes.c_uint)]
     lib.kf_take_device_error.restype = ctypes.c_int
     lib.kf_version.restype = ctypes.c_int
@@ -335,6 +337,11 @@ KF_DEVERR_TIMEOUT = 1
 def kf_set_step_kernel(mode: int) -> None:
     """C-ABI kf_set_step_kernel: KF_STEP_AUTO / KF_STEP_DIRECT / KF_STEP_STAGED."""
     _check(load().kf_set_step_kernel(int(mode)))
+
+
+def kf_set_staged_ctas_per_sm(ctas: int) -> None:
+    """C-ABI kf_set_staged_ctas_per_sm: 1..3 CTAs per SM under KF_STEP_STAGED, 0 = default."""
+    _check(load().kf_set_staged_ctas_per_sm(int(ctas)))
 
 
 def kf_take_device_error() -> int:

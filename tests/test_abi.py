@@ -54,3 +54,24 @@ def test_binding_refuses_cpu_tensors(lib):
     with pytest.raises(ValueError):
         kf.kf_p2z_propagate_update(kf.make_params(3.8), kf.make_layout(0, 0, 1), t, t, t, t,
                                    torch.zeros(1, dtype=torch.int8), t, t, t)
+
+
+def test_tuning_cache_text_round_trip(lib):
+    # the cache is host state: import / export / clear need no GPU
+    kf.autotune_clear()
+    assert kf.autotune_export() == ""
+    line = f"NVIDIA GB300/152|0|1|0|0|5|20|{kf.KF_STEP_STAGED}|256|3|0.0451\n"
+    kf.autotune_import(line)
+    assert kf.autotune_export() == line
+    bad_fields = ["no separators here", "G|0|1|0|0|5|20|9|256|2|0.1",  # unknown kernel
+                  "G|0|1|0|0|5|20|2|100|2|0.1",                       # CTA size
+                  "G|0|1|0|0|5|20|2|256|4|0.1",                       # CTAs per SM
+                  "G|2|1|0|0|5|20|2|256|2|0.1",                       # op
+                  "G|0|1|9|0|5|20|2|256|2|0.1",                       # precision
+                  "G|0|1|0|0|5|20|2|256|2"]                           # missing field
+    for bad in bad_fields:
+        with pytest.raises(kf.KfError):
+            kf.autotune_import(bad + "\n")
+    assert kf.autotune_export() == line
+    kf.autotune_clear()
+    assert kf.autotune_export() == ""

@@ -215,6 +215,22 @@ def test_adaptive_redo_pass_in_place(dev, step_kernel, layout):
     assert not np.any(ref[2] & 0x80)
 
 
+def test_adaptive_with_unaligned_status(dev):
+    # the redo pass reads status 16 bytes at a time where it can, byte by
+    # byte where the array is not 16-byte aligned or at its ragged end
+    w = grazing_p2r()
+    b = run(w, dev, (kf.KF_SOA, 0), kf.KF_ADAPTIVE)
+    ref = b.download()
+    big = torch.zeros(w.n + 16, dtype=torch.uint8, device=dev)
+    status = big[3:3 + w.n]
+    so, co = torch.empty_like(b.state_out), torch.empty_like(b.cov_out)
+    kf.kf_p2r_propagate_update(kf.make_params(w.bz, kf.KF_ADAPTIVE), b.layout, b.state_in,
+                               b.cov_in, so, co, b.charge, b.hit, b.hit_cov, b.surf, 1, status)
+    torch.cuda.synchronize()
+    assert torch.equal(so, b.state_out) and torch.equal(co, b.cov_out)
+    assert np.array_equal(status.cpu().numpy(), ref[2])
+
+
 def test_adaptive_needs_a_status_array(dev):
     w = W.make_p2r(1, 256, seed=5)
     b = kf.upload(w, kf.KF_AOSOA, 32, dev)
@@ -391,3 +407,54 @@ def test_compressed_covariance_step(dev, w_prec, layout):
         rep = compare.compare(g_st.T[idx], g_cov.T[idx], status.cpu().numpy()[idx], o_st, o_cv,
                               o_stat)
         assert rep["ok"], rep
+
+
+def run_compressed(w, dev, layout, precision, in_place=False):
+    lay = kf.make_layout(layout[0], layout[1], w.n)
+    sig, rho = W.compress_cov(w.cov)
+    st_in = kf.to_device(w.state, lay, dev)
+    sg_in = kf.to_device(sig, lay, dev)
+    rh_in = kf.to_device_half(rho, lay, dev)
+    if in_place:
+        st_out, sg_out, rh_out = st_in, sg_in, rh_in
+    else:
+        st_out, sg_out, rh_out = (torch.empty_like(st_in), torch.empty_like(sg_in),
+                                  torch.empty_like(rh_in))
+    status = torch.zeros(w.n, dtype=torch.uint8, device=dev)
+    kind = kf.KF_P2Z if w.kind == W.P2Z else kf.KF_P2R
+    per_track = np.ndim(w.surf) > 0
+    surf = torch.from_numpy(np.atleast_1d(np.asarray(w.surf, dtype=np.float32))).to(dev)
+    kf.kf_propagate_update_compressed(
+        kind, kf.make_params(w.bz, precision), lay, st_in, sg_in, rh_in, st_out, sg_out, rh_out,
+        torch.from_numpy(w.charge).to(dev), kf.to_device(w.hit, lay, dev),
+        kf.to_device(w.hitcov, lay, dev), surf, int(per_track), status)
+    torch.cuda.synchronize()
+    g_st = kf.from_device(st_out, 6, w.n, lay)
+    g_sig = kf.from_device(sg_out, 6, w.n, lay)
+    rh = rh_out.cpu().numpy()
+    if lay.kind == kf.KF_AOSOA:
+        rh = W.from_aosoa(rh.reshape(W.aosoa_blocks(w.n, lay.width), 15, lay.width), w.n)
+    else:
+        rh = rh.reshape(15, w.n)
+    return g_st, W.decompress_cov(g_sig, rh), status.cpu().numpy()
+
+
+def test_compressed_adaptive_redo_pass(dev):
+    # the compressed store with KF_ADAPTIVE on grazing crossings: marked
+    # tracks are decoded again from their untouched inputs and redone in
+    # FP64, in place as out of place; the result is within the bounds
+    w = grazing_p2r()
+    lay = (kf.KF_AOSOA, 32)
+    g = run_compressed(w, dev, lay, kf.KF_ADAPTIVE)
+    g2 = run_compressed(w, dev, lay, kf.KF_ADAPTIVE, in_place=True)
+    f32 = run_compressed(w, dev, lay, kf.KF_FP32)
+    for x, y in zip(g, g2):
+        assert np.array_equal(x, y)
+    assert np.any(g[1] != f32[1]) and not np.any(g[2] & 0x80)
+    sig, rho = W.compress_cov(w.cov)
+    c_in = W.decompress_cov(sig, rho)
+    o_st, o_cv, o_stat, _ = oracle.step_batch(w.kind, w.state.T, c_in.T, w.charge, w.hit.T,
+                                              w.hitcov.T, w.surf, w.bz, threads=8)
+    on_cyl = (o_stat & oracle.NO_INTERSECT) == 0
+    rep = compare.compare(g[0].T, g[1].T, g[2], o_st, o_cv, o_stat, on_cylinder=on_cyl)
+    assert rep["ok"], rep
