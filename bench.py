@@ -333,6 +333,10 @@ def chain_bench(args, kf, W, dev, rank):
     plain_fn = plain_graph.replay if plain_graph is not None else dc.run_plain
     timed(plain_fn, 2)
     plain_ms = timed(plain_fn, reps)
+    # the fused chain under KF_ADAPTIVE (FP32, FP64 redo of ill-conditioned layers)
+    ada_fn = lambda: dc.run(kf.KF_ADAPTIVE)
+    timed(ada_fn, 2)
+    adaptive_ms = timed(ada_fn, reps)
     # algorithmic bytes per track: fused reads state, cov, charge once (109 B),
     # hits + hit covariances per layer (36 B each), writes state + cov (108 B);
     # plain launches move 253 B per track per layer
@@ -344,6 +348,7 @@ def chain_bench(args, kf, W, dev, rank):
             "fused_ms": fused_ms, "fused_tracks_per_s": cw.n / (fused_ms * 1e-3),
             "plain_ms": plain_ms, "plain_tracks_per_s": cw.n / (plain_ms * 1e-3),
             "speedup": plain_ms / fused_ms,
+            "fused_adaptive_ms": adaptive_ms,
             "fused_GBps": fused_b * cw.n / (fused_ms * 1e-3) / 1e9,
             "plain_GBps": plain_b * cw.n / (plain_ms * 1e-3) / 1e9,
             "bytes_per_track": {"fused": fused_b, "plain": plain_b},
@@ -411,7 +416,9 @@ def serving_bench(args, kf, W, dev, rank):
         st = srv.stats()
         return arrivals, {"rate_events_per_s": rate, "tracks_per_s": tracks / (t_end - t0),
                           "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"], "max_ms": st["max_ms"],
-                          "batches": st["batches"], "max_batch_events": st["max_batch_events"]}
+                          "batches": st["batches"], "max_batch_events": st["max_batch_events"],
+                          "phases_ms": {ph: [st[f"{ph}_p50_ms"], st[f"{ph}_p99_ms"]]
+                                        for ph in ("queue", "ready", "compute", "out")}}
 
     runs = [serve(rate, 12 + rank + k) for k, rate in enumerate(args.serve_rates)]
     srv.close()

@@ -100,12 +100,12 @@ typedef struct {
                                correlations the update divides out).  Other
                                tracks run at the FP32 cost.  The single-step
                                entry points on device arrays (and the
-                               compressed one) need a status array with it:
-                               the FP32 kernel marks ill-conditioned tracks
-                               there and a second, short kernel redoes just
-                               those (KF_ERR_ARG when status is NULL).  The
-                               host-array entry points, the chain and the
-                               server take it without that restriction.     */
+                               compressed one) and the chain need a status
+                               array with it: the FP32 kernel marks
+                               ill-conditioned tracks there and a second,
+                               short kernel redoes just those (KF_ERR_ARG
+                               when status is NULL).  The host-array entry
+                               points and the server use their own.         */
 
 typedef struct {
     float    bz;        /* field along +z in tesla                          */
@@ -260,6 +260,7 @@ typedef struct {
  *                   at hit_covs + l * F6 floats
  *   layers          HOST array of L layer descriptors, 0 <= L <= KF_MAX_LAYERS
  *   status          [n] uint8: OR of the per-layer status bits, or NULL
+ *                   (not NULL with KF_ADAPTIVE)
  *   stream          cudaStream_t
  * A layer the track does not reach is skipped (KF_NO_INTERSECT is set, the
  * track is left as it was) and the chain goes on with the next layer; a
@@ -340,8 +341,10 @@ typedef struct {
     float   ms;           /* measured time per call of the chosen shape     */
 } kf_tuning;
 
-/* Time every candidate (3 warm-up + 10 timed calls each, synchronous) with
- * the arguments of kf_p2z/p2r_propagate_update, store and return the best.
+/* Time every candidate with the arguments of kf_p2z/p2r_propagate_update
+ * (synchronous; candidates take turns over 5 rounds of 10 timed calls after
+ * 3 warm-up calls, each judged by its median round), store and return the
+ * best.
  * Outputs are written repeatedly; with in == out the step is applied more
  * than once, so pass separate output arrays. */
 int kf_autotune_step(int32_t kind, const kf_params *params, kf_layout layout,
@@ -409,6 +412,13 @@ typedef struct {
     int64_t batches;                   /* kernel launches                      */
     int64_t max_batch_events;          /* most events in one launch            */
     double  p50_ms, p99_ms, max_ms, mean_ms; /* submit -> results in host memory */
+    /* The same latency split into phases, p50 and p99 of each (ms, as the
+     * scheduler thread observes them): queue = submit -> admitted (copy-in
+     * issued); ready = admitted -> its batch launched (copy-in, then waiting
+     * for the running batch); compute = launched -> batch seen finished;
+     * out = copy-out issued -> landed in host memory. */
+    double  queue_p50_ms, queue_p99_ms, ready_p50_ms, ready_p99_ms;
+    double  compute_p50_ms, compute_p99_ms, out_p50_ms, out_p99_ms;
 } kf_server_stats;
 
 /* Arena bytes one event of n tracks and L layers occupies (-1 if invalid). */

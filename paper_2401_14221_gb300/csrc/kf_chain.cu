@@ -54,14 +54,51 @@ __global__ void __launch_bounds__(256) chain_kernel(const ChainArgs a) {
   for (int e = 0; e < 21; ++e) C[e] = a.cov[l21.base + e * l21.stride];
   const float qf = (float)__ldg(a.charge + i);
 
-  unsigned st = chain_track<VARIANT>(p, C, qf, a.bz, a.L, a.kinds, a.pos, a.hits, a.hit_stride,
-                                     a.hitcovs, a.hc_stride, l3, l6);
+  unsigned st;
+  if constexpr (VARIANT == kAdaptive) {
+    st = chain_track_marking(p, C, qf, a.bz, a.L, a.kinds, a.pos, a.hits, a.hit_stride, a.hitcovs,
+                             a.hc_stride, l3, l6);
+    if (st & kRedo) {  // left to chain_redo_kernel, inputs untouched
+      a.status[i] = (uint8_t)kRedo;
+      return;
+    }
+  } else {
+    st = chain_track<VARIANT>(p, C, qf, a.bz, a.L, a.kinds, a.pos, a.hits, a.hit_stride,
+                              a.hitcovs, a.hc_stride, l3, l6);
+  }
   st |= finite_status(p, C);
 #pragma unroll
   for (int c = 0; c < 6; ++c) a.state[l6.base + c * l6.stride] = p[c];
 #pragma unroll
   for (int e = 0; e < 21; ++e) a.cov[l21.base + e * l21.stride] = C[e];
   if (a.status) a.status[i] = (uint8_t)st;
+}
+
+// KF_ADAPTIVE's second pass: tracks marked kRedo run the whole chain again
+// from their inputs, in FP32 with an FP64 redo of each ill-conditioned layer.
+// Each thread checks 16 status bytes.
+__global__ void __launch_bounds__(256) chain_redo_kernel(const ChainArgs a) {
+  const int64_t base = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * 16;
+  if (base >= a.n) return;
+  uint8_t m[16];
+  if (!(load_status16(a.status, base, a.n, m) & kRedo)) return;
+  for (int j = 0; j < 16; ++j) {
+    if (!(m[j] & kRedo)) continue;
+    const int64_t i = base + j;
+    const ChainLoc l6 = chain_locate<6>(i, a.n, a.soa, a.lw);
+    const ChainLoc l21 = chain_locate<21>(i, a.n, a.soa, a.lw);
+    const ChainLoc l3 = chain_locate<3>(i, a.n, a.soa, a.lw);
+    float p[6], C[21];
+    for (int c = 0; c < 6; ++c) p[c] = a.state[l6.base + c * l6.stride];
+    for (int e = 0; e < 21; ++e) C[e] = a.cov[l21.base + e * l21.stride];
+    const float qf = (float)a.charge[i];
+    unsigned st = chain_track<kAdaptive>(p, C, qf, a.bz, a.L, a.kinds, a.pos, a.hits,
+                                         a.hit_stride, a.hitcovs, a.hc_stride, l3, l6);
+    st |= finite_status(p, C);
+    for (int c = 0; c < 6; ++c) a.state[l6.base + c * l6.stride] = p[c];
+    for (int e = 0; e < 21; ++e) a.cov[l21.base + e * l21.stride] = C[e];
+    a.status[i] = (uint8_t)st;
+  }
 }
 
 }  // namespace
@@ -101,6 +138,8 @@ extern "C" int kf_kalman_chain(const kf_params *params, kf_layout layout, float 
   if (int rc = check_device_range(hit_covs, 4 * f6 * L, "hit_covs")) return rc;
   if (status)
     if (int rc = check_device_range(status, d.n, "status")) return rc;
+  if (!status && params->precision == KF_ADAPTIVE)
+    return set_error(KF_ERR_ARG, "KF_ADAPTIVE needs a status array (its redo pass reads it)");
 
   a.state = state;
   a.cov = cov;
@@ -133,5 +172,8 @@ extern "C" int kf_kalman_chain(const kf_params *params, kf_layout layout, float 
     case KF_FP64: chain_kernel<kFP64><<<(unsigned)blocks, threads, 0, s>>>(a); break;
     default: chain_kernel<kAdaptive><<<(unsigned)blocks, threads, 0, s>>>(a); break;
   }
-  return check_cuda(cudaGetLastError(), "chain launch");
+  if (int rc = check_cuda(cudaGetLastError(), "chain launch")) return rc;
+  if (params->precision != KF_ADAPTIVE) return KF_OK;
+  chain_redo_kernel<<<(unsigned)((d.n + 256 * 16 - 1) / (256 * 16)), 256, 0, s>>>(a);
+  return check_cuda(cudaGetLastError(), "chain redo pass launch");
 }

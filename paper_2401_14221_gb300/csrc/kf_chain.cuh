@@ -63,4 +63,50 @@ __device__ __forceinline__ unsigned chain_track(float (&p)[6], float (&C)[21], f
   return st;
 }
 
+// KF_ADAPTIVE's first pass: the chain in FP32 that gives up on the track at
+// the first ill-conditioned layer and returns kRedo (p and C are then
+// scratch; the caller stores nothing, so the track's inputs stay intact for
+// the redo pass).  Other tracks finish here at the FP32 cost, with no FP64
+// code in this kernel's register allocation.
+__device__ __forceinline__ unsigned chain_track_marking(float (&p)[6], float (&C)[21], float qf,
+                                                        float bz, int L, const int32_t *kinds,
+                                                        const float *pos, const float *hits,
+                                                        int64_t hit_stride, const float *hitcovs,
+                                                        int64_t hc_stride, const ChainLoc &l3,
+                                                        const ChainLoc &l6) {
+  unsigned st = 0;
+  LayerHit next;
+  load_layer_hit(hits, hit_stride, hitcovs, hc_stride, 0, l3, l6, next);
+  for (int l = 0; l < L; ++l) {
+    const LayerHit h = next;
+    if (l + 1 < L) load_layer_hit(hits, hit_stride, hitcovs, hc_stride, l + 1, l3, l6, next);
+    const unsigned sl =
+        kinds[l] == kP2z
+            ? p2z_step<kAdaptive>(p, C, qf, bz, pos[l], h.hx, h.hy, h.hc[0], h.hc[1], h.hc[2])
+            : p2r_step<kAdaptive>(p, C, qf, bz, pos[l], h.hx, h.hy, h.hz, h.hc);
+    if (sl & kRedo) return kRedo;
+    st |= sl;
+  }
+  return st;
+}
+
+// Status bytes base .. base+15 of an [n] array, one 16-byte load where the
+// array is 16-byte aligned and the run is whole, byte loads otherwise.
+__device__ __forceinline__ unsigned load_status16(const uint8_t *status, int64_t base, int64_t n,
+                                                  uint8_t (&m)[16]) {
+  if (base + 16 <= n && (reinterpret_cast<uintptr_t>(status) & 15u) == 0) {
+    const uint4 v = *reinterpret_cast<const uint4 *>(status + base);
+    const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+    for (int j = 0; j < 16; ++j) m[j] = (uint8_t)(w[j >> 2] >> (8 * (j & 3)));
+  } else {
+#pragma unroll
+    for (int j = 0; j < 16; ++j) m[j] = base + j < n ? status[base + j] : 0;
+  }
+  unsigned any = 0;
+#pragma unroll
+  for (int j = 0; j < 16; ++j) any |= m[j];
+  return any;
+}
+
 }  // namespace kf

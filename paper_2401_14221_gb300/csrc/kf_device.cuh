@@ -63,6 +63,10 @@ struct Fp<float> {
   static __device__ __forceinline__ float atan2_(float y, float x) { return atan2f(y, x); }
   static __device__ __forceinline__ float abs_(float x) { return fabsf(x); }
   static __device__ __forceinline__ float rint_(float x) { return rintf(x); }
+  // Quotients of well-scaled operands (|b| far below 2^126): the fast
+  // reciprocal-based division, within 2 ulp, instead of the IEEE sequence.
+  static __device__ __forceinline__ float div_(float a, float b) { return __fdividef(a, b); }
+  static __device__ __forceinline__ float rcp_(float b) { return __fdividef(1.0f, b); }
 };
 
 template <>
@@ -80,6 +84,8 @@ struct Fp<double> {
   static __device__ __forceinline__ double atan2_(double y, double x) { return atan2(y, x); }
   static __device__ __forceinline__ double abs_(double x) { return fabs(x); }
   static __device__ __forceinline__ double rint_(double x) { return rint(x); }
+  static __device__ __forceinline__ double div_(double a, double b) { return a / b; }
+  static __device__ __forceinline__ double rcp_(double b) { return 1.0 / b; }
 };
 
 // Packed lower-triangular index of a symmetric matrix element.
@@ -129,7 +135,7 @@ __device__ __forceinline__ T wrap_phi(T a) {
 // S(h) = sin(h)/h given sin(h); S(0) = 1.
 template <class T>
 __device__ __forceinline__ T sinc_from(T h, T sh) {
-  return Fp<T>::abs_(h) < T(1e-4) ? Fp<T>::fma_(-h * h, T(1) / T(6), T(1)) : sh / h;
+  return Fp<T>::abs_(h) < T(1e-4) ? Fp<T>::fma_(-h * h, T(1) / T(6), T(1)) : Fp<T>::div_(sh, h);
 }
 
 // dS/dh = (cos(h) - S(h)) / h; the difference cancels for small |h|, where
@@ -143,7 +149,7 @@ __device__ __forceinline__ T dsinc_from(T h, T ch, T S) {
                                    T(1) / T(30)),
                        T(-1) / T(3));
   }
-  return (ch - S) / h;
+  return F::div_(ch - S, h);
 }
 
 // C' = J C J^T for packed symmetric C, with J's structure fixed by NZ/ONE.
@@ -210,7 +216,8 @@ __device__ __forceinline__ bool propagate_to_z(const T (&in)[6], T qf, T bz, T z
   F::sincos_(phi, &sp, &cp);
   F::sincos_(th, &st, &ct);
   if (!(F::abs_(ct) > T(1e-4))) return false;
-  const T tanth = st / ct;
+  const T ict = F::rcp_(ct);
+  const T tanth = st * ict;
   const T dz = zt - z;
   const T s = dz * tanth;                 // transverse path to the plane
   const T dwdk = -qf * F::alpha * bz;     // d omega / d k
@@ -239,7 +246,7 @@ __device__ __forceinline__ bool propagate_to_z(const T (&in)[6], T qf, T bz, T z
   const T Xk = hs2 * (dS * cpm - S * spm);
   const T Yk = hs2 * (dS * spm + S * cpm);
   const T dsz = -tanth;
-  const T dsth = dz / (ct * ct);
+  const T dsth = dz * ict * ict;
 #pragma unroll
   for (int e = 0; e < 36; ++e) J[e] = T(0);
   J[0 * 6 + 2] = cp1 * dsz;
@@ -293,8 +300,9 @@ __device__ __forceinline__ bool propagate_to_r(const T (&in)[6], T qf, T bz, T R
   const T sh = yv * inv;                  // sin(h)
   const T h = F::atan2_(yv, xv);          // half turning angle
   const T L = T(2) * d * inv;             // chord
-  const T s = F::abs_(omega) > T(1e-12) ? T(2) * h / omega : d / den;
-  const T cot = ct / st;
+  const T s = F::abs_(omega) > T(1e-12) ? F::div_(T(2) * h, omega) : F::div_(d, den);
+  const T ist = F::rcp_(st);
+  const T cot = ct * ist;
   const T S = sinc_from(h, sh);
   const T dS = dsinc_from(h, ch, S);
   const T cpm = cp * ch - sp * sh;
@@ -320,7 +328,7 @@ __device__ __forceinline__ bool propagate_to_r(const T (&in)[6], T qf, T bz, T R
   // s(p) from g = x'^2 + y'^2 - R^2 = 0: ds/dp = -(x' dx'/dp + y' dy'/dp) / (x' cos + y' sin).
   const T gs = F::fma_(x1, cp1, y1 * sp1);
   rcos = gs;
-  const T ig = T(-1) / gs;
+  const T ig = -F::rcp_(gs);
   const T dsx = ig * x1;
   const T dsy = ig * y1;
   const T dsk = ig * F::fma_(x1, Xk, y1 * Yk);
@@ -339,7 +347,7 @@ __device__ __forceinline__ bool propagate_to_r(const T (&in)[6], T qf, T bz, T R
   J[2 * 6 + 1] = cot * dsy;
   J[2 * 6 + 3] = cot * dsk;
   J[2 * 6 + 4] = cot * dsphi;
-  J[2 * 6 + 5] = -s / (st * st);
+  J[2 * 6 + 5] = -s * ist * ist;
   J[4 * 6 + 0] = omega * dsx;
   J[4 * 6 + 1] = omega * dsy;
   J[4 * 6 + 3] = F::fma_(omega, dsk, s * dwdk);
@@ -408,7 +416,7 @@ __device__ __forceinline__ unsigned kalman_update(T (&p)[6], T (&C)[21], const T
   } else {
     const T det = F::fma_(S00, S11, -S01 * S01);
     if (!(S00 > T(0)) || !(det > T(0))) return kSNotPD;
-    const T inv = T(1) / det;
+    const T inv = F::rcp_(det);
     const T Si00 = S11 * inv, Si01 = -S01 * inv, Si11 = S00 * inv;
     T K0[6], K1[6];
 #pragma unroll
@@ -457,7 +465,7 @@ __device__ __forceinline__ unsigned kalman_update(T (&p)[6], T (&C)[21], const T
     } else {
       const T G00 = F::fma_(Si00, V00, Si01 * V01), G01 = F::fma_(Si00, V01, Si01 * V11);
       const T G10 = F::fma_(Si01, V00, Si11 * V01), G11 = F::fma_(Si01, V01, Si11 * V11);
-      const T ih0 = T(1) / h0;
+      const T ih0 = F::rcp_(h0);
 #pragma unroll
       for (int i = 0; i < 6; ++i) {
         if (i == SKIP) continue;

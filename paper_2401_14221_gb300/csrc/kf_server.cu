@@ -86,14 +86,52 @@ __global__ void __launch_bounds__(256) batch_chain_kernel(const __grid_constant_
 #pragma unroll
   for (int k = 0; k < 21; ++k) C[k] = e.cov[l21.base + k * l21.stride];
   const float qf = (float)__ldg(e.charge + i);
-  unsigned st = chain_track<VARIANT>(p, C, qf, a.bz, a.L, a.kinds, a.pos, e.hits, 3 * e.n,
-                                     e.hitcovs, 6 * e.n, l3, l6);
+  unsigned st;
+  if constexpr (VARIANT == kAdaptive) {
+    st = chain_track_marking(p, C, qf, a.bz, a.L, a.kinds, a.pos, e.hits, 3 * e.n, e.hitcovs,
+                             6 * e.n, l3, l6);
+    if (st & kRedo) {  // left to batch_redo_kernel, inputs untouched
+      e.status[i] = (uint8_t)kRedo;
+      return;
+    }
+  } else {
+    st = chain_track<VARIANT>(p, C, qf, a.bz, a.L, a.kinds, a.pos, e.hits, 3 * e.n, e.hitcovs,
+                              6 * e.n, l3, l6);
+  }
   st |= finite_status(p, C);
 #pragma unroll
   for (int c = 0; c < 6; ++c) e.state[l6.base + c * l6.stride] = p[c];
 #pragma unroll
   for (int k = 0; k < 21; ++k) e.cov[l21.base + k * l21.stride] = C[k];
   if (e.status) e.status[i] = (uint8_t)st;
+}
+
+// KF_ADAPTIVE's second pass over a batch: same grid as batch_chain_kernel;
+// each thread whose track is marked kRedo reruns the chain (FP32 with an
+// FP64 redo of each ill-conditioned layer).  The arena's status array is
+// always present.
+__global__ void __launch_bounds__(256) batch_redo_kernel(const __grid_constant__ BatchArgs a) {
+  int lo = 0, hi = a.nev - 1;
+  const int64_t b = blockIdx.x;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (a.ev[mid].block_begin <= b) lo = mid;
+    else hi = mid - 1;
+  }
+  const EventDesc &e = a.ev[lo];
+  const int64_t i = (b - e.block_begin) * blockDim.x + threadIdx.x;
+  if (i >= e.n || !(e.status[i] & kRedo)) return;
+  const ChainLoc l6{i, e.n}, l21{i, e.n}, l3{i, e.n};
+  float p[6], C[21];
+  for (int c = 0; c < 6; ++c) p[c] = e.state[l6.base + c * l6.stride];
+  for (int k = 0; k < 21; ++k) C[k] = e.cov[l21.base + k * l21.stride];
+  const float qf = (float)e.charge[i];
+  unsigned st = chain_track<kAdaptive>(p, C, qf, a.bz, a.L, a.kinds, a.pos, e.hits, 3 * e.n,
+                                       e.hitcovs, 6 * e.n, l3, l6);
+  st |= finite_status(p, C);
+  for (int c = 0; c < 6; ++c) e.state[l6.base + c * l6.stride] = p[c];
+  for (int k = 0; k < 21; ++k) e.cov[l21.base + k * l21.stride] = C[k];
+  e.status[i] = (uint8_t)st;
 }
 
 int64_t align256(int64_t x) { return (x + 255) & ~int64_t(255); }
@@ -132,7 +170,7 @@ struct Request {
   int64_t off = -1;  // arena offset
   Layout lay{};
   cudaEvent_t ev = nullptr;  // copies in / copies out landed
-  std::chrono::steady_clock::time_point t_submit, t_done;
+  std::chrono::steady_clock::time_point t_submit, t_admit, t_launch, t_finished, t_done;
 };
 
 // First-fit allocator over [0, size) with coalescing.
@@ -192,6 +230,7 @@ struct kf_server {
   int in_flight = 0;  // admitted, not yet done
   // statistics
   std::vector<double> latencies_ms;
+  std::vector<double> phase_ms[4];  // queue, ready, compute, out
   int64_t tracks_done = 0, batches = 0, max_batch_events = 0;
 };
 
@@ -284,9 +323,13 @@ bool launch_batch(kf_server *s, std::vector<Request *> &batch) {
       case KF_FP64_UPDATE: batch_chain_kernel<kFP64Update><<<g, 256, 0, s->s_compute>>>(a); break;
       case KF_JOSEPH: batch_chain_kernel<kJoseph><<<g, 256, 0, s->s_compute>>>(a); break;
       case KF_FP64: batch_chain_kernel<kFP64><<<g, 256, 0, s->s_compute>>>(a); break;
-      default: batch_chain_kernel<kAdaptive><<<g, 256, 0, s->s_compute>>>(a); break;
+      default:
+        batch_chain_kernel<kAdaptive><<<g, 256, 0, s->s_compute>>>(a);
+        e = cudaGetLastError();
+        if (e == cudaSuccess) batch_redo_kernel<<<g, 256, 0, s->s_compute>>>(a);
+        break;
     }
-    e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaGetLastError();
   }
   if (e == cudaSuccess) e = cudaEventRecord(s->batch_ev, s->s_compute);
   if (e != cudaSuccess) {
@@ -312,8 +355,14 @@ bool schedule_once(kf_server *s) {
     if (q != cudaSuccess) fail_locked(s, q, "server copy-out completion");
     r->t_done = std::chrono::steady_clock::now();
     r->phase = Phase::kDone;
-    s->latencies_ms.push_back(
-        std::chrono::duration<double, std::milli>(r->t_done - r->t_submit).count());
+    auto ms = [](std::chrono::steady_clock::time_point a, std::chrono::steady_clock::time_point b) {
+      return std::chrono::duration<double, std::milli>(b - a).count();
+    };
+    s->latencies_ms.push_back(ms(r->t_submit, r->t_done));
+    s->phase_ms[0].push_back(ms(r->t_submit, r->t_admit));
+    s->phase_ms[1].push_back(ms(r->t_admit, r->t_launch));
+    s->phase_ms[2].push_back(ms(r->t_launch, r->t_finished));
+    s->phase_ms[3].push_back(ms(r->t_finished, r->t_done));
     s->tracks_done += r->n;
     s->arena.release(r->off, r->lay.bytes);
     s->event_pool.push_back(r->ev);
@@ -328,7 +377,9 @@ bool schedule_once(kf_server *s) {
     const cudaError_t q = cudaEventQuery(s->batch_ev);
     if (q != cudaErrorNotReady) {
       if (q != cudaSuccess) fail_locked(s, q, "server batch completion");
+      const auto now = std::chrono::steady_clock::now();
       for (Request *r : s->running) {
+        r->t_finished = now;
         if (start_copy_out(s, r)) {
           r->phase = Phase::kReturning;
           s->returning.push_back(r);
@@ -347,6 +398,7 @@ bool schedule_once(kf_server *s) {
     const int64_t off = s->arena.alloc(r->lay.bytes);
     if (off < 0) break;  // wait for space: first come, first served
     r->off = off;
+    r->t_admit = std::chrono::steady_clock::now();
     r->ev = s->event_pool.back();
     s->event_pool.pop_back();
     s->pending.pop_front();
@@ -369,7 +421,11 @@ bool schedule_once(kf_server *s) {
       }
     }
     if (!batch.empty() && launch_batch(s, batch)) {
-      for (Request *r : batch) r->phase = Phase::kRunning;
+      const auto now = std::chrono::steady_clock::now();
+      for (Request *r : batch) {
+        r->phase = Phase::kRunning;
+        r->t_launch = now;
+      }
       s->running = batch;
       s->batch_in_flight = true;
       moved = true;
@@ -559,6 +615,17 @@ extern "C" int kf_server_get_stats(kf_server *s, kf_server_stats *out) {
     for (double x : v) sum += x;
     out->mean_ms = sum / (double)v.size();
   }
+  double *dst[4][2] = {{&out->queue_p50_ms, &out->queue_p99_ms},
+                       {&out->ready_p50_ms, &out->ready_p99_ms},
+                       {&out->compute_p50_ms, &out->compute_p99_ms},
+                       {&out->out_p50_ms, &out->out_p99_ms}};
+  for (int k = 0; k < 4; ++k) {
+    std::vector<double> w = s->phase_ms[k];
+    if (w.empty()) continue;
+    std::sort(w.begin(), w.end());
+    *dst[k][0] = w[std::min(w.size() - 1, (size_t)(0.50 * (w.size() - 1) + 0.5))];
+    *dst[k][1] = w[std::min(w.size() - 1, (size_t)(0.99 * (w.size() - 1) + 0.5))];
+  }
   return KF_OK;
 }
 
@@ -568,6 +635,7 @@ extern "C" int kf_server_reset_stats(kf_server *s) {
   if (!s) return set_error(KF_ERR_ARG, "server is NULL");
   std::lock_guard<std::mutex> lock(s->mu);
   s->latencies_ms.clear();
+  for (auto &w : s->phase_ms) w.clear();
   s->tracks_done = s->batches = s->max_batch_events = 0;
   return KF_OK;
 }

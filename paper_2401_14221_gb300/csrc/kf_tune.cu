@@ -16,6 +16,8 @@
 #include <string>
 #include <tuple>
 
+#include <algorithm>
+
 #include <cuda_runtime.h>
 
 #include "kf_common.cuh"
@@ -137,17 +139,26 @@ extern "C" int kf_autotune_step(int32_t kind, const kf_params *params, kf_layout
                            {KF_STEP_STAGED, 256, 3}};
   const int ncand = d.soa ? 2 : 5;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
+  // Candidates take turns over kRounds rounds (so that clock or memory
+  // drift during tuning hits all of them alike); each keeps its median.
+  constexpr int kRounds = 5;
+  float ms_of[5][kRounds];
+  for (int round = 0; round < kRounds; ++round) {
+    for (int c = 0; c < ncand; ++c) {
+      set_thread_override(&cands[c]);
+      const int rc = time_calls(call, s, round == 0 ? 3 : 1, 10, &ms_of[c][round]);
+      set_thread_override(nullptr);
+      if (rc) return rc;
+    }
+  }
   int best = -1;
   float best_ms = 0.0f;
   for (int c = 0; c < ncand; ++c) {
-    set_thread_override(&cands[c]);
-    float ms = 0.0f;
-    const int rc = time_calls(call, s, 3, 10, &ms);
-    set_thread_override(nullptr);
-    if (rc) return rc;
-    if (best < 0 || ms < best_ms) {
+    std::sort(ms_of[c], ms_of[c] + kRounds);
+    const float med = ms_of[c][kRounds / 2];
+    if (best < 0 || med < best_ms) {
       best = c;
-      best_ms = ms;
+      best_ms = med;
     }
   }
   tune_store(kOpStep, kind, params->precision, d.soa, d.lw, d.n, cands[best], best_ms);

@@ -65,7 +65,11 @@ class kf_server_stats(ctypes.Structure):
     _fields_ = [("events_done", ctypes.c_int64), ("tracks_done", ctypes.c_int64),
                 ("batches", ctypes.c_int64), ("max_batch_events", ctypes.c_int64),
                 ("p50_ms", ctypes.c_double), ("p99_ms", ctypes.c_double),
-                ("max_ms", ctypes.c_double), ("mean_ms", ctypes.c_double)]
+                ("max_ms", ctypes.c_double), ("mean_ms", ctypes.c_double),
+                ("queue_p50_ms", ctypes.c_double), ("queue_p99_ms", ctypes.c_double),
+                ("ready_p50_ms", ctypes.c_double), ("ready_p99_ms", ctypes.c_double),
+                ("compute_p50_ms", ctypes.c_double), ("compute_p99_ms", ctypes.c_double),
+                ("out_p50_ms", ctypes.c_double), ("out_p99_ms", ctypes.c_double)]
 
 
 _lib = None

@@ -111,3 +111,33 @@ def test_empty_chain_and_bad_layers(dev):
         kf.kf_kalman_chain(kf.make_params(cw.bz), dc.layout, dc.state, dc.cov, dc.charge,
                            dc.hits, dc.hit_covs, bad)
     assert e.value.code == kf.KF_ERR_ARG
+
+
+def test_adaptive_chain_redo_pass(dev, chain_full):
+    # KF_ADAPTIVE: the FP32 chain kernel gives up on a track at its first
+    # ill-conditioned layer and leaves it (inputs untouched) to a second
+    # kernel, which reruns the chain with an FP64 redo of such layers.  Some
+    # tracks of this workload cross layers at grazing incidence.
+    cw = chain_full
+    dc = kf.chain_upload(cw, kf.KF_AOSOA, 32, dev)
+    dc.run(kf.KF_FP32)
+    f32 = dc.download()
+    dc.reset()
+    dc.run(kf.KF_ADAPTIVE)
+    ada = dc.download()
+    assert not np.any(ada[2] & 0x80)
+    redone = np.any(ada[1] != f32[1], axis=0)
+    assert 0 < int(redone.sum()) < cw.n // 10
+    # tracks no layer marked are bitwise the FP32 chain
+    assert np.array_equal(ada[0][:, ~redone], f32[0][:, ~redone])
+    # the oracle on the redone tracks
+    idx = np.flatnonzero(redone)[:2000]
+    o_st, o_cv, o_stat = oracle_chain(cw, idx, oracle.FORM_STANDARD)
+    rep = compare.compare(ada[0].T[idx], ada[1].T[idx], ada[2][idx], o_st, o_cv, o_stat,
+                          on_cylinder=ends_on_cylinder(cw, o_st))
+    assert rep["ok"], rep
+    # the status array is required
+    with pytest.raises(kf.KfError) as e:
+        kf.kf_kalman_chain(kf.make_params(cw.bz, kf.KF_ADAPTIVE), dc.layout, dc.state, dc.cov,
+                           dc.charge, dc.hits, dc.hit_covs, dc.layers, None)
+    assert e.value.code == kf.KF_ERR_ARG
