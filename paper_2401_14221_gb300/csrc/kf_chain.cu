@@ -62,6 +62,9 @@ __global__ void __launch_bounds__(256) chain_kernel(const ChainArgs a) {
       a.status[i] = (uint8_t)kRedo;
       return;
     }
+  } else if constexpr (VARIANT == kFP64) {
+    st = chain_track_fp64(p, C, qf, a.bz, a.L, a.kinds, a.pos, a.hits, a.hit_stride, a.hitcovs,
+                          a.hc_stride, l3, l6);
   } else {
     st = chain_track<VARIANT>(p, C, qf, a.bz, a.L, a.kinds, a.pos, a.hits, a.hit_stride,
                               a.hitcovs, a.hc_stride, l3, l6);
@@ -75,8 +78,8 @@ __global__ void __launch_bounds__(256) chain_kernel(const ChainArgs a) {
 }
 
 // KF_ADAPTIVE's second pass: tracks marked kRedo run the whole chain again
-// from their inputs, in FP32 with an FP64 redo of each ill-conditioned layer.
-// Each thread checks 16 status bytes.
+// from their inputs in double (chain_track_fp64).  Each thread checks 16
+// status bytes.
 __global__ void __launch_bounds__(256) chain_redo_kernel(const ChainArgs a) {
   const int64_t base = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * 16;
   if (base >= a.n) return;
@@ -92,8 +95,8 @@ __global__ void __launch_bounds__(256) chain_redo_kernel(const ChainArgs a) {
     for (int c = 0; c < 6; ++c) p[c] = a.state[l6.base + c * l6.stride];
     for (int e = 0; e < 21; ++e) C[e] = a.cov[l21.base + e * l21.stride];
     const float qf = (float)a.charge[i];
-    unsigned st = chain_track<kAdaptive>(p, C, qf, a.bz, a.L, a.kinds, a.pos, a.hits,
-                                         a.hit_stride, a.hitcovs, a.hc_stride, l3, l6);
+    unsigned st = chain_track_fp64(p, C, qf, a.bz, a.L, a.kinds, a.pos, a.hits, a.hit_stride,
+                                   a.hitcovs, a.hc_stride, l3, l6);
     st |= finite_status(p, C);
     for (int c = 0; c < 6; ++c) a.state[l6.base + c * l6.stride] = p[c];
     for (int e = 0; e < 21; ++e) a.cov[l21.base + e * l21.stride] = C[e];

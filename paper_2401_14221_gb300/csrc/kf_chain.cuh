@@ -40,15 +40,18 @@ __device__ __forceinline__ void load_layer_hit(const float *hits, int64_t hit_st
   for (int c = 0; c < 6; ++c) h.hc[c] = __ldg(cp + c * l6.stride);
 }
 
-// Run one track (p, C in registers) through layers 0..L-1; the next layer's
-// hit is loaded while the current layer computes.  Returns the OR of the
-// per-layer status bits.
+// Run one track (p, C in registers) through layers 0..L-1 in float
+// arithmetic (kFP32, kJoseph, kFP64Update); the next layer's hit is loaded
+// while the current layer computes.  Returns the OR of the per-layer status
+// bits.
 template <int VARIANT>
 __device__ __forceinline__ unsigned chain_track(float (&p)[6], float (&C)[21], float qf, float bz,
                                                 int L, const int32_t *kinds, const float *pos,
                                                 const float *hits, int64_t hit_stride,
                                                 const float *hitcovs, int64_t hc_stride,
                                                 const ChainLoc &l3, const ChainLoc &l6) {
+  static_assert(VARIANT == kFP32 || VARIANT == kJoseph || VARIANT == kFP64Update,
+                "float-state chain variants only");
   unsigned st = 0;
   LayerHit next;
   load_layer_hit(hits, hit_stride, hitcovs, hc_stride, 0, l3, l6, next);
@@ -56,18 +59,54 @@ __device__ __forceinline__ unsigned chain_track(float (&p)[6], float (&C)[21], f
     const LayerHit h = next;
     if (l + 1 < L) load_layer_hit(hits, hit_stride, hitcovs, hc_stride, l + 1, l3, l6, next);
     if (kinds[l] == kP2z)
-      st |= p2z_step_inplace<VARIANT>(p, C, qf, bz, pos[l], h.hx, h.hy, h.hc[0], h.hc[1], h.hc[2]);
+      st |= p2z_step<VARIANT>(p, C, qf, bz, pos[l], h.hx, h.hy, h.hc[0], h.hc[1], h.hc[2]);
     else
-      st |= p2r_step_inplace<VARIANT>(p, C, qf, bz, pos[l], h.hx, h.hy, h.hz, h.hc);
+      st |= p2r_step<VARIANT>(p, C, qf, bz, pos[l], h.hx, h.hy, h.hz, h.hc);
   }
+  return st;
+}
+
+// The whole chain in double: the state and covariance are converted once,
+// kept in double registers across all layers and converted back once.  No
+// FP32 rounding happens between layers -- a crossing at grazing incidence
+// amplifies any error in its input by 1/cos(incidence), which reached 250 on
+// the outermost barrel layer for tracks that barely reach it.  Serves
+// kFP64 and the redo pass of kAdaptive.
+__device__ __forceinline__ unsigned chain_track_fp64(float (&pf)[6], float (&Cf)[21], float qf,
+                                                     float bz, int L, const int32_t *kinds,
+                                                     const float *pos, const float *hits,
+                                                     int64_t hit_stride, const float *hitcovs,
+                                                     int64_t hc_stride, const ChainLoc &l3,
+                                                     const ChainLoc &l6) {
+  double p[6], C[21];
+  for (int c = 0; c < 6; ++c) p[c] = pf[c];
+  for (int e = 0; e < 21; ++e) C[e] = Cf[e];
+  unsigned st = 0;
+  for (int l = 0; l < L; ++l) {
+    LayerHit h;
+    load_layer_hit(hits, hit_stride, hitcovs, hc_stride, l, l3, l6, h);
+    double hc[6], shrink, rcos;
+    for (int c = 0; c < 6; ++c) hc[c] = h.hc[c];
+    if (kinds[l] == kP2z)
+      st |= p2z_step_t<double, kStandard>(p, C, (double)qf, (double)bz, (double)pos[l],
+                                          (double)h.hx, (double)h.hy, hc[0], hc[1], hc[2],
+                                          shrink);
+    else
+      st |= p2r_step_t<double, kStandard>(p, C, (double)qf, (double)bz, (double)pos[l],
+                                          (double)h.hx, (double)h.hy, (double)h.hz, hc, shrink,
+                                          rcos);
+  }
+  for (int c = 0; c < 6; ++c) pf[c] = (float)p[c];
+  for (int e = 0; e < 21; ++e) Cf[e] = (float)C[e];
   return st;
 }
 
 // KF_ADAPTIVE's first pass: the chain in FP32 that gives up on the track at
 // the first ill-conditioned layer and returns kRedo (p and C are then
 // scratch; the caller stores nothing, so the track's inputs stay intact for
-// the redo pass).  Other tracks finish here at the FP32 cost, with no FP64
-// code in this kernel's register allocation.
+// the redo pass, which reruns the whole chain with chain_track_fp64).  Other
+// tracks finish here at the FP32 cost, with no FP64 code in this kernel's
+// register allocation.
 __device__ __forceinline__ unsigned chain_track_marking(float (&p)[6], float (&C)[21], float qf,
                                                         float bz, int L, const int32_t *kinds,
                                                         const float *pos, const float *hits,

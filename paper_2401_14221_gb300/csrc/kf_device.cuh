@@ -654,35 +654,8 @@ __device__ __forceinline__ unsigned step_variant(float (&p)[6], float (&C)[21], 
   }
 }
 
-// The same for callers that keep the step's input only in registers (the
-// chain): keep a copy and redo in place.
-template <int KIND, int VARIANT>
-__device__ __forceinline__ unsigned step_variant_inplace(float (&p)[6], float (&C)[21], float qf,
-                                                         float bz, float surf, float hx, float hy,
-                                                         float hz, const float (&hc)[6]) {
-  if constexpr (VARIANT == kAdaptive) {
-    float p0[6], C0[21];
-#pragma unroll
-    for (int i = 0; i < 6; ++i) p0[i] = p[i];
-#pragma unroll
-    for (int e = 0; e < 21; ++e) C0[e] = C[e];
-    unsigned st = step_variant<KIND, VARIANT>(p, C, qf, bz, surf, hx, hy, hz, hc);
-    if (st & kRedo) {
-#pragma unroll
-      for (int i = 0; i < 6; ++i) p[i] = p0[i];
-#pragma unroll
-      for (int e = 0; e < 21; ++e) C[e] = C0[e];
-      st = step_in_double<KIND>(p, C, qf, bz, surf, hx, hy, hz, hc);
-    }
-    return st;
-  } else {
-    return step_variant<KIND, VARIANT>(p, C, qf, bz, surf, hx, hy, hz, hc);
-  }
-}
-
 // Convenience entry points used by the kernels.  Under kAdaptive the
-// returned status may carry kRedo (see step_variant); the *_inplace forms
-// never return it.
+// returned status may carry kRedo (see step_variant).
 template <int VARIANT>
 __device__ __forceinline__ unsigned p2z_step(float (&p)[6], float (&C)[21], float qf, float bz,
                                              float zt, float hx, float hy, float vxx, float vxy,
@@ -696,21 +669,6 @@ __device__ __forceinline__ unsigned p2r_step(float (&p)[6], float (&C)[21], floa
                                              float R, float hx, float hy, float hz,
                                              const float (&hc)[6]) {
   return step_variant<kP2r, VARIANT>(p, C, qf, bz, R, hx, hy, hz, hc);
-}
-
-template <int VARIANT>
-__device__ __forceinline__ unsigned p2z_step_inplace(float (&p)[6], float (&C)[21], float qf,
-                                                     float bz, float zt, float hx, float hy,
-                                                     float vxx, float vxy, float vyy) {
-  const float hc[6] = {vxx, vxy, vyy, 0.0f, 0.0f, 0.0f};
-  return step_variant_inplace<kP2z, VARIANT>(p, C, qf, bz, zt, hx, hy, 0.0f, hc);
-}
-
-template <int VARIANT>
-__device__ __forceinline__ unsigned p2r_step_inplace(float (&p)[6], float (&C)[21], float qf,
-                                                     float bz, float R, float hx, float hy,
-                                                     float hz, const float (&hc)[6]) {
-  return step_variant_inplace<kP2r, VARIANT>(p, C, qf, bz, R, hx, hy, hz, hc);
 }
 
 // Non-finite check over the written result (any NaN/Inf poisons the sum;

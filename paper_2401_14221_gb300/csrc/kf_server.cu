@@ -94,6 +94,9 @@ __global__ void __launch_bounds__(256) batch_chain_kernel(const __grid_constant_
       e.status[i] = (uint8_t)kRedo;
       return;
     }
+  } else if constexpr (VARIANT == kFP64) {
+    st = chain_track_fp64(p, C, qf, a.bz, a.L, a.kinds, a.pos, e.hits, 3 * e.n, e.hitcovs,
+                          6 * e.n, l3, l6);
   } else {
     st = chain_track<VARIANT>(p, C, qf, a.bz, a.L, a.kinds, a.pos, e.hits, 3 * e.n, e.hitcovs,
                               6 * e.n, l3, l6);
@@ -107,9 +110,8 @@ __global__ void __launch_bounds__(256) batch_chain_kernel(const __grid_constant_
 }
 
 // KF_ADAPTIVE's second pass over a batch: same grid as batch_chain_kernel;
-// each thread whose track is marked kRedo reruns the chain (FP32 with an
-// FP64 redo of each ill-conditioned layer).  The arena's status array is
-// always present.
+// each thread whose track is marked kRedo reruns the whole chain in double
+// (chain_track_fp64).  The arena's status array is always present.
 __global__ void __launch_bounds__(256) batch_redo_kernel(const __grid_constant__ BatchArgs a) {
   int lo = 0, hi = a.nev - 1;
   const int64_t b = blockIdx.x;
@@ -126,8 +128,8 @@ __global__ void __launch_bounds__(256) batch_redo_kernel(const __grid_constant__
   for (int c = 0; c < 6; ++c) p[c] = e.state[l6.base + c * l6.stride];
   for (int k = 0; k < 21; ++k) C[k] = e.cov[l21.base + k * l21.stride];
   const float qf = (float)e.charge[i];
-  unsigned st = chain_track<kAdaptive>(p, C, qf, a.bz, a.L, a.kinds, a.pos, e.hits, 3 * e.n,
-                                       e.hitcovs, 6 * e.n, l3, l6);
+  unsigned st = chain_track_fp64(p, C, qf, a.bz, a.L, a.kinds, a.pos, e.hits, 3 * e.n,
+                                 e.hitcovs, 6 * e.n, l3, l6);
   st |= finite_status(p, C);
   for (int c = 0; c < 6; ++c) e.state[l6.base + c * l6.stride] = p[c];
   for (int k = 0; k < 21; ++k) e.cov[l21.base + k * l21.stride] = C[k];

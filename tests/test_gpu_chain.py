@@ -53,10 +53,11 @@ def ends_on_cylinder(cw, o_st):
 
 @pytest.mark.parametrize("kind", [W.P2Z, W.P2R])
 @pytest.mark.parametrize("layout", [(kf.KF_SOA, 0), (kf.KF_AOSOA, 32)])
-def test_chain_of_one_layer_equals_single_step_bitwise(dev, kind, layout):
+@pytest.mark.parametrize("precision", [kf.KF_FP32, kf.KF_FP64, kf.KF_ADAPTIVE])
+def test_chain_of_one_layer_equals_single_step_bitwise(dev, kind, layout, precision):
     w = W.make_p2z(20011, seed=41) if kind == W.P2Z else W.make_p2r(1, 20011, seed=41)
     b = kf.upload(w, layout[0], layout[1], dev)
-    b.run()
+    b.run(precision)
     ref = b.download()
     cw = W.ChainWorkload(n=w.n, bz=w.bz, kinds=np.array([kind], dtype=np.int32),
                          pos=np.array([w.surf], dtype=np.float32), event_sizes=np.array([w.n]),
@@ -64,7 +65,7 @@ def test_chain_of_one_layer_equals_single_step_bitwise(dev, kind, layout):
                          hitcov=w.hitcov[None], truth_pool_layers=np.zeros((1, 6, 1)),
                          truth_index=np.zeros(w.n, dtype=np.int64))
     dc = kf.chain_upload(cw, layout[0], layout[1], dev)
-    dc.run()
+    dc.run(precision)
     got = dc.download()
     for a, c in zip(ref, got):
         assert np.array_equal(a, c)
@@ -116,8 +117,9 @@ def test_empty_chain_and_bad_layers(dev):
 def test_adaptive_chain_redo_pass(dev, chain_full):
     # KF_ADAPTIVE: the FP32 chain kernel gives up on a track at its first
     # ill-conditioned layer and leaves it (inputs untouched) to a second
-    # kernel, which reruns the chain with an FP64 redo of such layers.  Some
-    # tracks of this workload cross layers at grazing incidence.
+    # kernel, which reruns the whole chain with the state in double.  Some
+    # tracks of this workload barely reach the outer barrel layers and cross
+    # them at grazing incidence (cos down to 0.004).
     cw = chain_full
     dc = kf.chain_upload(cw, kf.KF_AOSOA, 32, dev)
     dc.run(kf.KF_FP32)
@@ -131,11 +133,11 @@ def test_adaptive_chain_redo_pass(dev, chain_full):
     # tracks no layer marked are bitwise the FP32 chain
     assert np.array_equal(ada[0][:, ~redone], f32[0][:, ~redone])
     # the oracle on the redone tracks
-    idx = np.flatnonzero(redone)[:2000]
+    idx = np.flatnonzero(redone)
     o_st, o_cv, o_stat = oracle_chain(cw, idx, oracle.FORM_STANDARD)
     rep = compare.compare(ada[0].T[idx], ada[1].T[idx], ada[2][idx], o_st, o_cv, o_stat,
                           on_cylinder=ends_on_cylinder(cw, o_st))
-    assert rep["ok"], rep
+    assert rep["ok"], {k: rep.get(k) for k in ("param", "cov", "worst_param", "worst_cov")}
     # the status array is required
     with pytest.raises(kf.KfError) as e:
         kf.kf_kalman_chain(kf.make_params(cw.bz, kf.KF_ADAPTIVE), dc.layout, dc.state, dc.cov,
