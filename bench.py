@@ -41,9 +41,11 @@ NEVTS, NTRKS, RADIUS = 100, 9600, 30.0
 BYTES_PER_TRACK_P2R = 253
 FALLBACK_HBM_GBS = 6800.0
 NOMINAL_HBM_GBS = 7900.0
-KERNEL_SOURCES = ("paper_2401_14221_gb300/csrc/kf_device.cuh",
+# what the staged step kernel is compiled from (the capture in profiles/ is
+# valid while these are unchanged)
+KERNEL_SOURCES = ("paper_2401_14221_gb300/csrc/kf_common.cuh",
+                  "paper_2401_14221_gb300/csrc/kf_device.cuh",
                   "paper_2401_14221_gb300/csrc/kf_step.cuh",
-                  "paper_2401_14221_gb300/csrc/kf_step.cu",
                   "paper_2401_14221_gb300/csrc/kf_step_staged.cu")
 
 
@@ -64,6 +66,8 @@ def parse():
                     help="skip the fused-chain vs per-layer-launch comparison")
     ap.add_argument("--chain-steps", type=int, default=10)
     ap.add_argument("--no-variants", action="store_true")
+    ap.add_argument("--no-scaling", action="store_true",
+                    help="skip the 240k / 3.84M batch-size context measurement")
     ap.add_argument("--no-serving", action="store_true",
                     help="skip the serving-loop measurement")
     ap.add_argument("--serve-events", type=int, default=2048)
@@ -531,15 +535,27 @@ def main():
 
     w = W.make_p2r(NEVTS, NTRKS, seed=shard.rank_seed(1, rank))
 
-    def time_launches(batches, reps):
+    def graph_time(batches, replays):
+        # one launch per batch captured in a CUDA graph, replayed; ms per launch
+        st = torch.cuda.Stream()
+        with torch.cuda.stream(st):
+            for b in batches:
+                b.run(stream=st)
         torch.cuda.synchronize()
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=st):
+            for b in batches:
+                b.run()
+        for _ in range(5):
+            g.replay()
+        torch.cuda.synchronize()
+        a, b_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a.record()
-        for i in range(reps):
-            batches[i % len(batches)].run()
-        b.record()
+        for _ in range(replays):
+            g.replay()
+        b_.record()
         torch.cuda.synchronize()
-        return a.elapsed_time(b) / reps
+        return a.elapsed_time(b_) / (replays * len(batches))
 
     # Kernel x layout sweep (outside the timed region): the direct kernel on
     # SoA and AoSoA, the staged kernel on AoSoA block widths.
@@ -559,8 +575,7 @@ def main():
                 kf.kf_set_step_kernel(mode)
                 # staged: 2 CTAs per SM x 3 stages; staged3: 3 x 2 stages
                 kf.kf_set_staged_ctas_per_sm(3 if mname == "staged3" else 2)
-                time_launches(bs, 20)
-                ms = time_launches(bs, 200)
+                ms = graph_time(bs, 100)
                 sweep[f"{mname}/{lname}"] = {"ms": ms, "tracks_per_s": w.n / (ms * 1e-3)}
             del bs
         best = min(sweep, key=lambda k: sweep[k]["ms"])
@@ -644,8 +659,29 @@ def main():
               "ms_per_step_sd": (sum((x - sum(reps) / 10) ** 2 for x in reps) / 9) ** 0.5,
               "ms_per_step_p50": 0.5 * (reps_sorted[4] + reps_sorted[5])}
 
-    # Roofline of the step kernel: algorithmic bytes / average launch time.
     peak, peak_src = measured_hbm_peak()
+    # Batch-size scaling of the same kernel (context: a fixed per-launch cost
+    # of ramp, tail and launch gap weighs less on larger batches).  The
+    # 960,000-track arrays are tiled to 4x; two buffer sets rotate.
+    scaling = []
+    if not args.no_scaling:
+        import dataclasses
+
+        import numpy as np
+        for mult, reps in ((0.25, 400), (4, 100)):
+            m = int(w.n * mult)
+            tile = (lambda a: np.tile(a, (1, 4))[:, :m]) if mult > 1 else (lambda a: a[:, :m])
+            wm = dataclasses.replace(w, n=m, state=tile(w.state), cov=tile(w.cov),
+                                     charge=np.tile(w.charge, 4)[:m], hit=tile(w.hit),
+                                     hitcov=tile(w.hitcov))
+            bm = [kf.upload(wm, kind, width, dev) for _ in range(2)]
+            ms_m = graph_time(bm, reps)
+            scaling.append({"tracks": m, "ms": ms_m, "tracks_per_s": m / (ms_m * 1e-3),
+                            "GBps": BYTES_PER_TRACK_P2R * m / (ms_m * 1e-3) / 1e9,
+                            "frac": BYTES_PER_TRACK_P2R * m / (ms_m * 1e-3) / 1e9 / peak})
+            del bm
+
+    # Roofline of the step kernel: algorithmic bytes / average launch time.
     achieved = BYTES_PER_TRACK_P2R * w.n / (ms_per_step * 1e-3) / 1e9
     traffic = profiled_traffic()
 
@@ -737,6 +773,7 @@ def main():
             "gpu_launches": args.steps,
             "clocks": clocks,
             "spread": spread,
+            "batch_scaling": scaling,
             "sweep": sweep,
             "autotune": tuned,
             "device_error": kf.kf_take_device_error(),

@@ -78,16 +78,15 @@ __global__ void __launch_bounds__(256) chain_kernel(const ChainArgs a) {
 }
 
 // KF_ADAPTIVE's second pass: tracks marked kRedo run the whole chain again
-// from their inputs in double (chain_track_fp64).  Each thread checks 16
-// status bytes.
+// from their inputs in double (chain_track_fp64).  Each block gathers the
+// marked tracks of its span first (gather_marked), so warps run full.
 __global__ void __launch_bounds__(256) chain_redo_kernel(const ChainArgs a) {
-  const int64_t base = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * 16;
-  if (base >= a.n) return;
-  uint8_t m[16];
-  if (!(load_status16(a.status, base, a.n, m) & kRedo)) return;
-  for (int j = 0; j < 16; ++j) {
-    if (!(m[j] & kRedo)) continue;
-    const int64_t i = base + j;
+  __shared__ int32_t list[kRedoSpan];
+  __shared__ int count;
+  const int64_t span0 = (int64_t)blockIdx.x * kRedoSpan;
+  const int cnt = gather_marked(a.status, span0, a.n, list, &count);
+  for (int q = threadIdx.x; q < cnt; q += blockDim.x) {
+    const int64_t i = span0 + list[q];
     const ChainLoc l6 = chain_locate<6>(i, a.n, a.soa, a.lw);
     const ChainLoc l21 = chain_locate<21>(i, a.n, a.soa, a.lw);
     const ChainLoc l3 = chain_locate<3>(i, a.n, a.soa, a.lw);
@@ -177,6 +176,6 @@ extern "C" int kf_kalman_chain(const kf_params *params, kf_layout layout, float 
   }
   if (int rc = check_cuda(cudaGetLastError(), "chain launch")) return rc;
   if (params->precision != KF_ADAPTIVE) return KF_OK;
-  chain_redo_kernel<<<(unsigned)((d.n + 256 * 16 - 1) / (256 * 16)), 256, 0, s>>>(a);
+  chain_redo_kernel<<<(unsigned)((d.n + kRedoSpan - 1) / kRedoSpan), 256, 0, s>>>(a);
   return check_cuda(cudaGetLastError(), "chain redo pass launch");
 }

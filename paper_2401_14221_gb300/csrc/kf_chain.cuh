@@ -129,23 +129,4 @@ __device__ __forceinline__ unsigned chain_track_marking(float (&p)[6], float (&C
   return st;
 }
 
-// Status bytes base .. base+15 of an [n] array, one 16-byte load where the
-// array is 16-byte aligned and the run is whole, byte loads otherwise.
-__device__ __forceinline__ unsigned load_status16(const uint8_t *status, int64_t base, int64_t n,
-                                                  uint8_t (&m)[16]) {
-  if (base + 16 <= n && (reinterpret_cast<uintptr_t>(status) & 15u) == 0) {
-    const uint4 v = *reinterpret_cast<const uint4 *>(status + base);
-    const uint32_t w[4] = {v.x, v.y, v.z, v.w};
-#pragma unroll
-    for (int j = 0; j < 16; ++j) m[j] = (uint8_t)(w[j >> 2] >> (8 * (j & 3)));
-  } else {
-#pragma unroll
-    for (int j = 0; j < 16; ++j) m[j] = base + j < n ? status[base + j] : 0;
-  }
-  unsigned any = 0;
-#pragma unroll
-  for (int j = 0; j < 16; ++j) any |= m[j];
-  return any;
-}
-
 }  // namespace kf

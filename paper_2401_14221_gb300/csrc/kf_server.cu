@@ -109,31 +109,59 @@ __global__ void __launch_bounds__(256) batch_chain_kernel(const __grid_constant_
   if (e.status) e.status[i] = (uint8_t)st;
 }
 
-// KF_ADAPTIVE's second pass over a batch: same grid as batch_chain_kernel;
-// each thread whose track is marked kRedo reruns the whole chain in double
-// (chain_track_fp64).  The arena's status array is always present.
-__global__ void __launch_bounds__(256) batch_redo_kernel(const __grid_constant__ BatchArgs a) {
+// KF_ADAPTIVE's second pass over a batch.  Block r covers batch-grid blocks
+// [16 r, 16 r + 16) (4,096 track slots, possibly of several events); it
+// gathers the slots whose track is marked kRedo into shared memory, then its
+// threads rerun those tracks' whole chain in double (chain_track_fp64), so
+// that warps run full.  The arena's status array is always present.
+constexpr int kBatchRedoBlocks = 16;
+
+__device__ __forceinline__ int batch_event_of(const BatchArgs &a, int64_t b) {
   int lo = 0, hi = a.nev - 1;
-  const int64_t b = blockIdx.x;
   while (lo < hi) {
     const int mid = (lo + hi + 1) >> 1;
     if (a.ev[mid].block_begin <= b) lo = mid;
     else hi = mid - 1;
   }
-  const EventDesc &e = a.ev[lo];
-  const int64_t i = (b - e.block_begin) * blockDim.x + threadIdx.x;
-  if (i >= e.n || !(e.status[i] & kRedo)) return;
-  const ChainLoc l6{i, e.n}, l21{i, e.n}, l3{i, e.n};
-  float p[6], C[21];
-  for (int c = 0; c < 6; ++c) p[c] = e.state[l6.base + c * l6.stride];
-  for (int k = 0; k < 21; ++k) C[k] = e.cov[l21.base + k * l21.stride];
-  const float qf = (float)e.charge[i];
-  unsigned st = chain_track_fp64(p, C, qf, a.bz, a.L, a.kinds, a.pos, e.hits, 3 * e.n,
-                                 e.hitcovs, 6 * e.n, l3, l6);
-  st |= finite_status(p, C);
-  for (int c = 0; c < 6; ++c) e.state[l6.base + c * l6.stride] = p[c];
-  for (int k = 0; k < 21; ++k) e.cov[l21.base + k * l21.stride] = C[k];
-  e.status[i] = (uint8_t)st;
+  return lo;
+}
+
+__global__ void __launch_bounds__(256) batch_redo_kernel(const __grid_constant__ BatchArgs a,
+                                                         int64_t nblocks) {
+  __shared__ int16_t ev_of[kBatchRedoBlocks * 256];
+  __shared__ int32_t idx_of[kBatchRedoBlocks * 256];
+  __shared__ int count;
+  if (threadIdx.x == 0) count = 0;
+  __syncthreads();
+  for (int h = 0; h < kBatchRedoBlocks; ++h) {
+    const int64_t b = (int64_t)blockIdx.x * kBatchRedoBlocks + h;
+    if (b >= nblocks) break;
+    const int ev = batch_event_of(a, b);
+    const EventDesc &e = a.ev[ev];
+    const int64_t i = (b - e.block_begin) * 256 + threadIdx.x;
+    if (i < e.n && (e.status[i] & kRedo)) {
+      const int q = atomicAdd(&count, 1);
+      ev_of[q] = (int16_t)ev;
+      idx_of[q] = (int32_t)i;
+    }
+  }
+  __syncthreads();
+  const int cnt = count;
+  for (int q = threadIdx.x; q < cnt; q += blockDim.x) {
+    const EventDesc &e = a.ev[ev_of[q]];
+    const int64_t i = idx_of[q];
+    const ChainLoc l6{i, e.n}, l21{i, e.n}, l3{i, e.n};
+    float p[6], C[21];
+    for (int c = 0; c < 6; ++c) p[c] = e.state[l6.base + c * l6.stride];
+    for (int k = 0; k < 21; ++k) C[k] = e.cov[l21.base + k * l21.stride];
+    const float qf = (float)e.charge[i];
+    unsigned st = chain_track_fp64(p, C, qf, a.bz, a.L, a.kinds, a.pos, e.hits, 3 * e.n,
+                                   e.hitcovs, 6 * e.n, l3, l6);
+    st |= finite_status(p, C);
+    for (int c = 0; c < 6; ++c) e.state[l6.base + c * l6.stride] = p[c];
+    for (int k = 0; k < 21; ++k) e.cov[l21.base + k * l21.stride] = C[k];
+    e.status[i] = (uint8_t)st;
+  }
 }
 
 int64_t align256(int64_t x) { return (x + 255) & ~int64_t(255); }
@@ -328,7 +356,9 @@ bool launch_batch(kf_server *s, std::vector<Request *> &batch) {
       default:
         batch_chain_kernel<kAdaptive><<<g, 256, 0, s->s_compute>>>(a);
         e = cudaGetLastError();
-        if (e == cudaSuccess) batch_redo_kernel<<<g, 256, 0, s->s_compute>>>(a);
+        if (e == cudaSuccess)
+          batch_redo_kernel<<<(g + kBatchRedoBlocks - 1) / kBatchRedoBlocks, 256, 0, s->s_compute>>>(
+              a, (int64_t)g);
         break;
     }
     if (e == cudaSuccess) e = cudaGetLastError();
@@ -513,7 +543,8 @@ extern "C" int kf_server_submit(kf_server *s, int64_t n, const float *state, con
   using namespace kf;
   clear_error();
   if (!s || !ticket) return set_error(KF_ERR_ARG, "server or ticket is NULL");
-  if (n < 1) return set_error(KF_ERR_ARG, "an event needs n >= 1 tracks");
+  if (n < 1 || n > 0x7fffffffLL)
+    return set_error(KF_ERR_ARG, "an event needs 1 <= n < 2^31 tracks");
   if (!state || !cov || !charge || !hits || !hit_covs || !state_out || !cov_out)
     return set_error(KF_ERR_ARG, "a required pointer is NULL");
   const kf::srv::Layout lay = kf::srv::event_layout(n, s->cfg.L);

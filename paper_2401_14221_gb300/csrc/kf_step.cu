@@ -79,37 +79,24 @@ __global__ void __launch_bounds__(256) step_kernel(const __grid_constant__ StepA
   if (a.status) a.status[i] = (uint8_t)st;
 }
 
-// The redo pass of KF_ADAPTIVE.  Each thread checks 16 consecutive status
-// bytes with one 16-byte load (byte loads where the array is not 16-byte
-// aligned or at the ragged end), so the scan costs one load per thread in a
-// single wave; only marked tracks run the FP64 step.
-constexpr int kRedoScan = 16;
-
+// The redo pass of KF_ADAPTIVE: each block gathers the marked tracks of its
+// span of kRedoSpan tracks (one 16-byte status load per 16 tracks), then its
+// threads run the FP64 step on them, 32 marked tracks to a warp.
 template <int KIND>
 __global__ void __launch_bounds__(256) redo_pass_kernel(const __grid_constant__ StepArgs a) {
-  const int64_t base = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * kRedoScan;
-  if (base >= a.n) return;
-  uint8_t m[kRedoScan];
-  if (base + kRedoScan <= a.n && (reinterpret_cast<uintptr_t>(a.status) & 15u) == 0) {
-    const uint4 v = *reinterpret_cast<const uint4 *>(a.status + base);
-    const uint32_t w[4] = {v.x, v.y, v.z, v.w};
-#pragma unroll
-    for (int j = 0; j < kRedoScan; ++j) m[j] = (uint8_t)(w[j >> 2] >> (8 * (j & 3)));
-  } else {
-#pragma unroll
-    for (int j = 0; j < kRedoScan; ++j) m[j] = base + j < a.n ? a.status[base + j] : 0;
+  __shared__ int32_t list[kRedoSpan];
+  __shared__ int count;
+  const int64_t span0 = (int64_t)blockIdx.x * kRedoSpan;
+  const int cnt = gather_marked(a.status, span0, a.n, list, &count);
+  for (int q = threadIdx.x; q < cnt; q += blockDim.x) {
+    const int64_t i = span0 + list[q];
+    a.status[i] = (uint8_t)redo_track_fp64<KIND>(a, i);
   }
-  unsigned any = 0;
-#pragma unroll
-  for (int j = 0; j < kRedoScan; ++j) any |= m[j];
-  if (!(any & kRedo)) return;
-  for (int j = 0; j < kRedoScan; ++j)
-    if (m[j] & kRedo) a.status[base + j] = (uint8_t)redo_track_fp64<KIND>(a, base + j);
 }
 
 int launch_redo_pass(int kind, const StepArgs &a, cudaStream_t s) {
   if (a.n == 0) return KF_OK;
-  const int64_t blocks = (a.n + 256 * kRedoScan - 1) / (256 * kRedoScan);
+  const int64_t blocks = (a.n + kRedoSpan - 1) / kRedoSpan;
   if (blocks > 0x7fffffffLL) return set_error(KF_ERR_ARG, "n too large for one launch");
   const unsigned g = (unsigned)blocks;
   if (kind == kP2z)

@@ -77,6 +77,52 @@ __device__ __forceinline__ unsigned redo_track_fp64(const StepArgs &a, int64_t i
   for (int e = 0; e < 21; ++e) __stcs(a.cov_out + b21 + e * s, Cf[e]);
   return st;
 }
+
+// Status bytes base .. base+15 of an [n] array, one 16-byte load where the
+// array is 16-byte aligned and the run is whole, byte loads otherwise.
+__device__ __forceinline__ unsigned load_status16(const uint8_t *status, int64_t base, int64_t n,
+                                                  uint8_t (&m)[16]) {
+  if (base + 16 <= n && (reinterpret_cast<uintptr_t>(status) & 15u) == 0) {
+    const uint4 v = *reinterpret_cast<const uint4 *>(status + base);
+    const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+    for (int j = 0; j < 16; ++j) m[j] = (uint8_t)(w[j >> 2] >> (8 * (j & 3)));
+  } else {
+#pragma unroll
+    for (int j = 0; j < 16; ++j) m[j] = base + j < n ? status[base + j] : 0;
+  }
+  unsigned any = 0;
+#pragma unroll
+  for (int j = 0; j < 16; ++j) any |= m[j];
+  return any;
+}
+
+// Redo passes gather the marked tracks of a span of kRedoSpan tracks into a
+// shared-memory list before running them, so that each warp runs 32 marked
+// tracks instead of one marked track among 31 idle lanes: GB300 issues an
+// FP64 warp instruction over many cycles whether or not its lanes are active.
+constexpr int kRedoPerThread = 32;
+constexpr int kRedoSpan = 256 * kRedoPerThread;  // tracks per 256-thread block
+
+// Fill list[0..count) with the offsets (from span0) of the tracks marked
+// kRedo among [span0, min(span0 + kRedoSpan, n)); returns the count.  Every
+// thread of the block must call it.
+__device__ __forceinline__ int gather_marked(const uint8_t *status, int64_t span0, int64_t n,
+                                             int32_t *list, int *count) {
+  if (threadIdx.x == 0) *count = 0;
+  __syncthreads();
+  for (int h = 0; h < kRedoPerThread / 16; ++h) {
+    const int64_t base = span0 + ((int64_t)h * blockDim.x + threadIdx.x) * 16;
+    if (base >= n) break;
+    uint8_t m[16];
+    if (load_status16(status, base, n, m) & kRedo)
+      for (int j = 0; j < 16; ++j)
+        if (m[j] & kRedo) list[atomicAdd(count, 1)] = (int32_t)(base - span0 + j);
+  }
+  __syncthreads();
+  return *count;
+}
+
 #endif
 
 // How a step (or chain) launch is shaped.

@@ -156,31 +156,16 @@ __global__ void __launch_bounds__(256)
 
 // KF_ADAPTIVE's second pass on the compressed store: tracks marked kRedo
 // are decoded again from their (untouched) inputs and stepped in FP64.  Each
-// thread checks 16 consecutive status bytes (one 16-byte load where aligned).
-constexpr int kRedoScan = 16;
-
+// block gathers the marked tracks of its span first, so warps run full.
 template <int KIND>
 __global__ void __launch_bounds__(256)
     redo_compressed_kernel(const __grid_constant__ CompressedArgs a) {
-  const int64_t base = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * kRedoScan;
-  if (base >= a.n) return;
-  uint8_t mk[kRedoScan];
-  if (base + kRedoScan <= a.n && (reinterpret_cast<uintptr_t>(a.status) & 15u) == 0) {
-    const uint4 v = *reinterpret_cast<const uint4 *>(a.status + base);
-    const uint32_t w[4] = {v.x, v.y, v.z, v.w};
-#pragma unroll
-    for (int j = 0; j < kRedoScan; ++j) mk[j] = (uint8_t)(w[j >> 2] >> (8 * (j & 3)));
-  } else {
-#pragma unroll
-    for (int j = 0; j < kRedoScan; ++j) mk[j] = base + j < a.n ? a.status[base + j] : 0;
-  }
-  unsigned any = 0;
-#pragma unroll
-  for (int j = 0; j < kRedoScan; ++j) any |= mk[j];
-  if (!(any & kRedo)) return;
-  for (int j = 0; j < kRedoScan; ++j) {
-    if (!(mk[j] & kRedo)) continue;
-    const int64_t i = base + j;
+  __shared__ int32_t list[kRedoSpan];
+  __shared__ int count;
+  const int64_t span0 = (int64_t)blockIdx.x * kRedoSpan;
+  const int cnt = gather_marked(a.status, span0, a.n, list, &count);
+  for (int q = threadIdx.x; q < cnt; q += blockDim.x) {
+    const int64_t i = span0 + list[q];
     const Loc l6 = locate<6>(i, a.n, a.soa, a.lw);
     const Loc l15 = locate<15>(i, a.n, a.soa, a.lw);
     const Loc l3 = locate<3>(i, a.n, a.soa, a.lw);
@@ -279,7 +264,7 @@ extern "C" int kf_propagate_update_compressed(
   }
   if (int rc = check_cuda(cudaGetLastError(), "compressed step launch")) return rc;
   if (params->precision != KF_ADAPTIVE) return KF_OK;
-  const unsigned gr = (unsigned)((d.n + 256 * kRedoScan - 1) / (256 * kRedoScan));
+  const unsigned gr = (unsigned)((d.n + kRedoSpan - 1) / kRedoSpan);
   if (kind == KF_P2Z)
     redo_compressed_kernel<kP2z><<<gr, threads, 0, s>>>(a);
   else

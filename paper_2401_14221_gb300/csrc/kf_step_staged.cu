@@ -182,6 +182,12 @@ __global__ void __launch_bounds__(kThreads, CTAS)
     mbar_fence_init();
   }
   __syncthreads();
+  // Programmatic dependent launch: let the next kernel on the stream be
+  // scheduled now (its CTAs take SMs as ours retire and set up their
+  // barriers), and wait here until the previous kernel has completed and its
+  // writes are visible -- nothing global is touched before this point.
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+  asm volatile("griddepcontrol.wait;" ::: "memory");
 
   if (warp == kComputeWarps) {
     // ------------------------------------------------------------ producer
@@ -290,8 +296,17 @@ int launch_w(const StepArgs &a, cudaStream_t s, int grid, int dev) {
       return rc;
     if (dev >= 0 && dev < 64) configured[dev] = true;
   }
-  kern<<<grid, kThreads, smem, s>>>(a);
-  return check_cuda(cudaGetLastError(), "staged step launch");
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)grid);
+  cfg.blockDim = dim3(kThreads);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return check_cuda(cudaLaunchKernelEx(&cfg, kern, a), "staged step launch");
 }
 
 template <int KIND, int VARIANT, int CTAS>
