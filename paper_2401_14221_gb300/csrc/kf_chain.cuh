@@ -27,18 +27,31 @@ struct LayerHit {
   float hx, hy, hz, hc[6];
 };
 
-__device__ __forceinline__ void load_layer_hit(const float *hits, int64_t hit_stride,
-                                               const float *hitcovs, int64_t hc_stride, int l,
-                                               const ChainLoc &l3, const ChainLoc &l6,
-                                               LayerHit &h) {
-  const float *hp = hits + l * hit_stride + l3.base;
-  const float *cp = hitcovs + l * hc_stride + l6.base;
-  h.hx = __ldg(hp);
-  h.hy = __ldg(hp + l3.stride);
-  h.hz = __ldg(hp + 2 * l3.stride);
+// Walks one track's hit and hit covariance through the layers: pointers to
+// the track's element of the current layer, advanced by the per-layer strides
+// (no index arithmetic per layer beyond two pointer increments).
+struct HitCursor {
+  const float *hp, *cp;
+  int64_t s3, s6, hit_stride, hc_stride;
+
+  __device__ __forceinline__ HitCursor(const float *hits, int64_t hit_stride_,
+                                       const float *hitcovs, int64_t hc_stride_,
+                                       const ChainLoc &l3, const ChainLoc &l6)
+      : hp(hits + l3.base), cp(hitcovs + l6.base), s3(l3.stride), s6(l6.stride),
+        hit_stride(hit_stride_), hc_stride(hc_stride_) {}
+
+  __device__ __forceinline__ void load(LayerHit &h) const {
+    h.hx = __ldg(hp);
+    h.hy = __ldg(hp + s3);
+    h.hz = __ldg(hp + 2 * s3);
 #pragma unroll
-  for (int c = 0; c < 6; ++c) h.hc[c] = __ldg(cp + c * l6.stride);
-}
+    for (int c = 0; c < 6; ++c) h.hc[c] = __ldg(cp + c * s6);
+  }
+  __device__ __forceinline__ void next_layer() {
+    hp += hit_stride;
+    cp += hc_stride;
+  }
+};
 
 // Run one track (p, C in registers) through layers 0..L-1 in float
 // arithmetic (kFP32, kJoseph, kFP64Update); the next layer's hit is loaded
@@ -53,11 +66,15 @@ __device__ __forceinline__ unsigned chain_track(float (&p)[6], float (&C)[21], f
   static_assert(VARIANT == kFP32 || VARIANT == kJoseph || VARIANT == kFP64Update,
                 "float-state chain variants only");
   unsigned st = 0;
+  HitCursor cur(hits, hit_stride, hitcovs, hc_stride, l3, l6);
   LayerHit next;
-  load_layer_hit(hits, hit_stride, hitcovs, hc_stride, 0, l3, l6, next);
+  cur.load(next);
   for (int l = 0; l < L; ++l) {
     const LayerHit h = next;
-    if (l + 1 < L) load_layer_hit(hits, hit_stride, hitcovs, hc_stride, l + 1, l3, l6, next);
+    if (l + 1 < L) {
+      cur.next_layer();
+      cur.load(next);
+    }
     if (kinds[l] == kP2z)
       st |= p2z_step<VARIANT>(p, C, qf, bz, pos[l], h.hx, h.hy, h.hc[0], h.hc[1], h.hc[2]);
     else
@@ -82,9 +99,10 @@ __device__ __forceinline__ unsigned chain_track_fp64(float (&pf)[6], float (&Cf)
   for (int c = 0; c < 6; ++c) p[c] = pf[c];
   for (int e = 0; e < 21; ++e) C[e] = Cf[e];
   unsigned st = 0;
-  for (int l = 0; l < L; ++l) {
+  HitCursor cur(hits, hit_stride, hitcovs, hc_stride, l3, l6);
+  for (int l = 0; l < L; ++l, cur.next_layer()) {
     LayerHit h;
-    load_layer_hit(hits, hit_stride, hitcovs, hc_stride, l, l3, l6, h);
+    cur.load(h);
     double hc[6], shrink, rcos;
     for (int c = 0; c < 6; ++c) hc[c] = h.hc[c];
     if (kinds[l] == kP2z)
@@ -114,11 +132,15 @@ __device__ __forceinline__ unsigned chain_track_marking(float (&p)[6], float (&C
                                                         int64_t hc_stride, const ChainLoc &l3,
                                                         const ChainLoc &l6) {
   unsigned st = 0;
+  HitCursor cur(hits, hit_stride, hitcovs, hc_stride, l3, l6);
   LayerHit next;
-  load_layer_hit(hits, hit_stride, hitcovs, hc_stride, 0, l3, l6, next);
+  cur.load(next);
   for (int l = 0; l < L; ++l) {
     const LayerHit h = next;
-    if (l + 1 < L) load_layer_hit(hits, hit_stride, hitcovs, hc_stride, l + 1, l3, l6, next);
+    if (l + 1 < L) {
+      cur.next_layer();
+      cur.load(next);
+    }
     const unsigned sl =
         kinds[l] == kP2z
             ? p2z_step<kAdaptive>(p, C, qf, bz, pos[l], h.hx, h.hy, h.hc[0], h.hc[1], h.hc[2])

@@ -361,6 +361,21 @@ def test_host_array_entry_matches_device_entry(dev, layout, pinned):
         assert rep["ok"], rep
 
 
+@pytest.mark.parametrize("n", [1, 33, 4097, 300001])
+@pytest.mark.parametrize("layout", [(kf.KF_SOA, 0), (kf.KF_AOSOA, 128)])
+def test_host_entry_default_chunk(dev, n, layout):
+    # the default chunk (262,144 tracks): one chunk, or two with the last
+    # one ragged
+    w = W.make_p2r(1, n, seed=18)
+    hb = kf.host_upload(w, layout[0], layout[1], dev, pinned=True)
+    hb.run()
+    torch.cuda.synchronize()
+    got = hb.download()
+    ref = run(w, dev, layout).download()
+    for a, c in zip(ref, got):
+        assert np.array_equal(a, c)
+
+
 def test_host_entry_rejects_small_workspace(dev):
     w = W.make_p2z(5000, seed=17)
     hb = kf.host_upload(w, kf.KF_SOA, 0, dev, chunk_tracks=1024)
