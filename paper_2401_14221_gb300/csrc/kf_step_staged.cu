@@ -7,8 +7,9 @@
 // a persistent CTA splits the two jobs:
 //
 //   * one producer warp streams tiles of T = 256 tracks into shared memory
-//     with cp.async.bulk (the Blackwell bulk-copy engine), S = 3 stages deep,
-//     each completion tracked by an mbarrier's transaction count;
+//     with cp.async.bulk (the Blackwell bulk-copy engine), S stages deep
+//     (3 with two CTAs per SM, 2 with three), each completion tracked by an
+//     mbarrier's transaction count;
 //   * eight compute warps take a staged tile, read their track's inputs from
 //     shared memory (bank-conflict-free for AoSoA), release the stage, and run
 //     the step in registers, writing results straight to global memory.
@@ -18,9 +19,13 @@
 // per-track surface are plain [n] arrays read directly (tiny, and a bulk copy
 // of a ragged tail could run past their end).  Every mbarrier wait is
 // bounded; on timeout the kernel records KF_DEVERR_TIMEOUT in a device error
-// word and leaves its loop, so a broken pipeline cannot hang the GPU.
+// word and leaves its loop, so a broken pipeline cannot hang the GPU; the
+// producer waits (bounded) for its last copies to land before it exits.
+// Launches use programmatic dependent launch: the next kernel on the stream
+// is scheduled while this one drains and waits for it on the GPU.
 #include <cuda_runtime.h>
 
+#include <atomic>
 #include <mutex>
 
 #include "kf_common.cuh"
@@ -192,6 +197,7 @@ __global__ void __launch_bounds__(kThreads, CTAS)
   if (warp == kComputeWarps) {
     // ------------------------------------------------------------ producer
     if (lane == 0) {
+      int64_t issued = 0;
       for (int64_t k = 0; k < ntiles; ++k) {
         const int s = (int)(k % kStages);
         const uint32_t ph = (uint32_t)(k / kStages) & 1u;
@@ -205,7 +211,12 @@ __global__ void __launch_bounds__(kThreads, CTAS)
         bulk_g2s(st + kStateB, a.cov_in + first * 21, cols * 21 * 4, &full[s]);
         bulk_g2s(st + kStateB + kCovB, a.hit + first * 3, cols * 3 * 4, &full[s]);
         bulk_g2s(st + kStateB + kCovB + kHitB, a.hitcov + first * 6, cols * 6 * 4, &full[s]);
+        issued = k + 1;
       }
+      // No copy may still be writing this CTA's shared memory when it exits
+      // (the compute warps have normally consumed them all already).
+      for (int64_t k = issued > kStages ? issued - kStages : 0; k < issued; ++k)
+        if (!mbar_wait(&full[k % kStages], (uint32_t)(k / kStages) & 1u)) break;
     }
     return;
   }
@@ -288,13 +299,13 @@ template <int KIND, int VARIANT, int W, int CTAS>
 int launch_w(const StepArgs &a, cudaStream_t s, int grid, int dev) {
   auto kern = step_staged_kernel<KIND, VARIANT, W, CTAS>;
   constexpr int smem = smem_bytes(CTAS);
-  static bool configured[64] = {};  // per instantiation and device
-  if (dev < 0 || dev >= 64 || !configured[dev]) {
+  static std::atomic<bool> configured[64] = {};  // per instantiation and device
+  if (dev < 0 || dev >= 64 || !configured[dev].load(std::memory_order_acquire)) {
     if (int rc = check_cuda(
             cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem),
             "cudaFuncSetAttribute"))
       return rc;
-    if (dev >= 0 && dev < 64) configured[dev] = true;
+    if (dev >= 0 && dev < 64) configured[dev].store(true, std::memory_order_release);
   }
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)grid);
