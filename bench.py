@@ -39,6 +39,12 @@ NEVTS, NTRKS, RADIUS = 100, 9600, 30.0
 # Algorithmic bytes per p2r track: read state 24 + cov 84 + charge 1 + hit 12
 # + hit cov 24 = 145, write state 24 + cov 84 = 108.
 BYTES_PER_TRACK_P2R = 253
+# FP32 operations per track and layer of the fused chain (FFMA counted twice,
+# FMUL, FADD), from the ncu thread-instruction counters of one chain launch
+# on 64 events (profiles/chain_kernel_fp32_64events.md)
+FLOPS_PER_TRACK_LAYER = 465
+# FP32 peak from the unit counts: 152 SMs x 128 FP32 lanes x 2 flops x clock
+FP32_LANES = 152 * 128
 FALLBACK_HBM_GBS = 6800.0
 NOMINAL_HBM_GBS = 7900.0
 # what the staged step kernel is compiled from (the capture in profiles/ is
@@ -346,8 +352,15 @@ def chain_bench(args, kf, W, dev, rank):
     # plain launches move 253 B per track per layer
     fused_b = 109 + 36 * L + 108
     plain_b = 253 * L
+    # the chain is issue-bound: its roofline is the FP32 arithmetic peak
+    fp32_peak = FP32_LANES * 2 * 2.07e9 / 1e12
+    achieved = FLOPS_PER_TRACK_LAYER * cw.n * L / (fused_ms * 1e-3) / 1e12
     return {"workload": f"{len(cw.event_sizes)} events, {cw.n} tracks (lognormal sizes, median "
                         f"5000, clipped 500-40000), {L} alternating layers",
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": fp32_peak,
+                         "unit": "TFLOP/s", "frac": achieved / fp32_peak,
+                         "flops_per_track_layer": FLOPS_PER_TRACK_LAYER,
+                         "peak_source": "152 SMs x 128 FP32 lanes x 2 flops x 2.07 GHz"},
             "tracks": cw.n, "layers": L,
             "fused_ms": fused_ms, "fused_tracks_per_s": cw.n / (fused_ms * 1e-3),
             "plain_ms": plain_ms, "plain_tracks_per_s": cw.n / (plain_ms * 1e-3),
