@@ -41,7 +41,7 @@ NEVTS, NTRKS, RADIUS = 100, 9600, 30.0
 BYTES_PER_TRACK_P2R = 253
 # FP32 operations per track and layer of the fused chain (FFMA counted twice,
 # FMUL, FADD), from the ncu thread-instruction counters of one chain launch
-# on 64 events (profiles/chain_kernel_fp32_64events.md)
+# on 64 events (bench.py --profile-only --kind chain, captured with ncu --set full)
 FLOPS_PER_TRACK_LAYER = 465
 # FP32 peak from the unit counts: 152 SMs x 128 FP32 lanes x 2 flops x clock
 FP32_LANES = 152 * 128
