@@ -360,7 +360,9 @@ def chain_bench(args, kf, W, dev, rank):
             "roofline": {"bound": "alu", "achieved": achieved, "peak": fp32_peak,
                          "unit": "TFLOP/s", "frac": achieved / fp32_peak,
                          "flops_per_track_layer": FLOPS_PER_TRACK_LAYER,
-                         "peak_source": "152 SMs x 128 FP32 lanes x 2 flops x 2.07 GHz"},
+                         "peak_source": "152 SMs x 128 FP32 lanes x 2 flops x 2.07 GHz",
+                         "frac_of_hbm": (109 + 36 * L + 108) * cw.n / (fused_ms * 1e-3) / 1e9
+                                        / measured_hbm_peak()[0]},
             "tracks": cw.n, "layers": L,
             "fused_ms": fused_ms, "fused_tracks_per_s": cw.n / (fused_ms * 1e-3),
             "plain_ms": plain_ms, "plain_tracks_per_s": cw.n / (plain_ms * 1e-3),
@@ -656,6 +658,13 @@ def main():
     ms_per_step = elapsed_ms / args.steps
     value = shard.whole_job_throughput(w.n, args.steps, world, elapsed_ms * 1e-3)
 
+    # The p2z single step on 8,192 tracks (the small configuration): latency
+    # of one launch, graph-replayed back to back
+    w_small = W.make_p2z(8192, seed=shard.rank_seed(1, rank))
+    small = [kf.upload(w_small, kind, width, dev) for _ in range(2)]
+    p2z_small_us = graph_time(small, 500) * 1e3
+    del small
+
     # Spread: ten timed repeats of a tenth of the steps each.
     reps = []
     kr = max(args.steps // 10, 4)
@@ -787,6 +796,7 @@ def main():
             "clocks": clocks,
             "spread": spread,
             "batch_scaling": scaling,
+            "p2z_8192_us_per_launch": p2z_small_us,
             "sweep": sweep,
             "autotune": tuned,
             "device_error": kf.kf_take_device_error(),

@@ -376,6 +376,30 @@ def test_host_entry_default_chunk(dev, n, layout):
         assert np.array_equal(a, c)
 
 
+@pytest.mark.parametrize("entry", ["workspace", "noalloc"])
+def test_host_entries_run_adaptive_without_a_status_array(dev, entry):
+    # KF_ADAPTIVE needs a status array on the device for its redo pass; the
+    # host-array entry points use their own staging for it, so the caller may
+    # pass none.  Results equal the device entry's bit for bit.
+    w = grazing_p2r()
+    lay = (kf.KF_AOSOA, 32)
+    ref = run(w, dev, lay, kf.KF_ADAPTIVE).download()
+    hb = kf.host_upload(w, lay[0], lay[1], dev, chunk_tracks=1024, pinned=True)
+    hb.state_out.fill_(np.nan)
+    params = kf.make_params(w.bz, kf.KF_ADAPTIVE)
+    if entry == "workspace":
+        kf.kf_p2r_propagate_update_host(params, hb.layout, hb.state_in, hb.cov_in, hb.state_out,
+                                        hb.cov_out, hb.charge, hb.hit, hb.hit_cov, hb.surf, 1,
+                                        None, hb.workspace, 1024)
+    else:
+        kf.kf_propagate_update_host_noalloc(kf.KF_P2R, params, hb.layout, hb.state_in,
+                                            hb.cov_in, hb.state_out, hb.cov_out, hb.charge,
+                                            hb.hit, hb.hit_cov, hb.surf, 1, None, 1024)
+    torch.cuda.synchronize()
+    got = hb.download()
+    assert np.array_equal(got[0], ref[0]) and np.array_equal(got[1], ref[1])
+
+
 def test_host_entry_rejects_small_workspace(dev):
     w = W.make_p2z(5000, seed=17)
     hb = kf.host_upload(w, kf.KF_SOA, 0, dev, chunk_tracks=1024)

@@ -112,11 +112,13 @@ def test_results_alone_equal_results_in_the_mix(dev, events):
         srv.close()
 
 
-def test_server_results_match_the_oracle(dev, events):
-    # the adaptive variant: FP64 redo of ill-conditioned layers (grazing
-    # crossings) keeps every track within the bounds
+@pytest.mark.parametrize("precision", [kf.KF_ADAPTIVE, kf.KF_FP64])
+def test_server_results_match_the_oracle(dev, events, precision):
+    # adaptive: tracks with an ill-conditioned layer (grazing crossings) run
+    # the whole chain again in double; FP64: every track in double.  Both
+    # keep every track within the bounds.
     cw = events
-    srv = make_server(cw, dev, 256 << 20, precision=kf.KF_ADAPTIVE)
+    srv = make_server(cw, dev, 256 << 20, precision=precision)
     try:
         for e in range(0, len(cw.event_sizes), 9):
             lo, hi, ins, outs = event_arrays(cw, e)
