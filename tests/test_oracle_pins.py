@@ -535,3 +535,23 @@ def test_chain_of_one_layer_is_the_single_step():
     st2, cv2, s2 = oracle.chain_batch([oracle.P2R], [w.surf], w.state.T, w.cov.T, w.charge,
                                       w.hit.T[None], w.hitcov.T[None], w.bz)
     assert np.array_equal(st1, st2) and np.array_equal(cv1, cv2) and np.array_equal(s1, s2)
+
+
+def test_oracle_regression_fixture():
+    # six fixed tracks stored by tests/golden/make_oracle_regression.py: the
+    # oracle must reproduce its stored outputs (guards against unnoticed
+    # change; the physics is pinned by the tests above)
+    import json
+    import os
+    path = os.path.join(os.path.dirname(__file__), "golden", "oracle_regression.json")
+    with open(path) as f:
+        cases = json.load(f)
+    assert len(cases) == 6
+    for c in cases:
+        kind = oracle.P2Z if c["kind"] == "p2z" else oracle.P2R
+        p2, c2, chi2, st = oracle.step(kind, c["state"], c["cov"], c["q"], c["hit"],
+                                       c["hit_cov"], c["bz"], c["surf"])
+        assert st == c["status"]
+        assert np.allclose(p2, c["state_out"], rtol=1e-12, atol=1e-15)
+        assert np.allclose(c2, c["cov_out"], rtol=1e-12, atol=1e-25)
+        assert abs(chi2 - c["chi2"]) <= 1e-10 * max(1.0, abs(c["chi2"]))
