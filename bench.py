@@ -39,6 +39,9 @@ NEVTS, NTRKS, RADIUS = 100, 9600, 30.0
 # Algorithmic bytes per p2r track: read state 24 + cov 84 + charge 1 + hit 12
 # + hit cov 24 = 145, write state 24 + cov 84 = 108.
 BYTES_PER_TRACK_P2R = 253
+# p2z reads hit x, y and hit covariance xx, xy, yy only: 24 + 84 + 1 + 8 + 12
+# read, 108 written
+BYTES_PER_TRACK_P2Z = 237
 # FP32 operations per track and layer of the fused chain (FFMA counted twice,
 # FMUL, FADD), from the ncu thread-instruction counters of one chain launch
 # on 64 events (bench.py --profile-only --kind chain, captured with ncu --set full)
@@ -659,11 +662,22 @@ def main():
     value = shard.whole_job_throughput(w.n, args.steps, world, elapsed_ms * 1e-3)
 
     # The p2z single step on 8,192 tracks (the small configuration): latency
-    # of one launch, graph-replayed back to back
+    # of one launch, graph-replayed back to back; and p2z at the p2r batch
+    # size (237 algorithmic bytes per track: hit z and three hit-covariance
+    # entries are not read)
     w_small = W.make_p2z(8192, seed=shard.rank_seed(1, rank))
     small = [kf.upload(w_small, kind, width, dev) for _ in range(2)]
     p2z_small_us = graph_time(small, 500) * 1e3
     del small
+    p2z_big = None
+    if not args.no_scaling:
+        w_z = W.make_p2z(w.n, seed=shard.rank_seed(2, rank))
+        bz_ = [kf.upload(w_z, kind, width, dev) for _ in range(4)]
+        ms_z = graph_time(bz_, 200)
+        p2z_big = {"tracks": w_z.n, "ms": ms_z, "tracks_per_s": w_z.n / (ms_z * 1e-3),
+                   "GBps": BYTES_PER_TRACK_P2Z * w_z.n / (ms_z * 1e-3) / 1e9,
+                   "bytes_per_track": BYTES_PER_TRACK_P2Z}
+        del bz_, w_z
 
     # Spread: ten timed repeats of a tenth of the steps each.
     reps = []
@@ -769,6 +783,8 @@ def main():
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(w)
 
+    if p2z_big is not None:
+        p2z_big["frac"] = p2z_big["GBps"] / peak
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
@@ -797,6 +813,7 @@ def main():
             "spread": spread,
             "batch_scaling": scaling,
             "p2z_8192_us_per_launch": p2z_small_us,
+            "p2z_960k": p2z_big,
             "sweep": sweep,
             "autotune": tuned,
             "device_error": kf.kf_take_device_error(),

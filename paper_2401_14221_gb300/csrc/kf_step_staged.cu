@@ -206,11 +206,26 @@ __global__ void __launch_bounds__(kThreads, CTAS)
         sch.tile(k, blockIdx.x, a.n, &first, &m);
         const uint32_t cols = (uint32_t)(((m + W - 1) / W) * W);  // whole blocks
         unsigned char *st = smem + s * kStageB;
-        mbar_arrive_expect_tx(&full[s], cols * (6 + 21 + 3 + 6) * 4);
-        bulk_g2s(st, a.state_in + first * 6, cols * 6 * 4, &full[s]);
-        bulk_g2s(st + kStateB, a.cov_in + first * 21, cols * 21 * 4, &full[s]);
-        bulk_g2s(st + kStateB + kCovB, a.hit + first * 3, cols * 3 * 4, &full[s]);
-        bulk_g2s(st + kStateB + kCovB + kHitB, a.hitcov + first * 6, cols * 6 * 4, &full[s]);
+        if (KIND == kP2r) {
+          mbar_arrive_expect_tx(&full[s], cols * (6 + 21 + 3 + 6) * 4);
+          bulk_g2s(st, a.state_in + first * 6, cols * 6 * 4, &full[s]);
+          bulk_g2s(st + kStateB, a.cov_in + first * 21, cols * 21 * 4, &full[s]);
+          bulk_g2s(st + kStateB + kCovB, a.hit + first * 3, cols * 3 * 4, &full[s]);
+          bulk_g2s(st + kStateB + kCovB + kHitB, a.hitcov + first * 6, cols * 6 * 4, &full[s]);
+        } else {
+          // p2z measures x, y only: per AoSoA block, copy hit rows x, y and
+          // hit-covariance rows xx, xy, yy (237 instead of 253 B per track)
+          const uint32_t nb = cols / W;
+          mbar_arrive_expect_tx(&full[s], cols * (6 + 21 + 2 + 3) * 4);
+          bulk_g2s(st, a.state_in + first * 6, cols * 6 * 4, &full[s]);
+          bulk_g2s(st + kStateB, a.cov_in + first * 21, cols * 21 * 4, &full[s]);
+          for (uint32_t b = 0; b < nb; ++b) {
+            bulk_g2s(st + kStateB + kCovB + b * 3 * W * 4, a.hit + (first + b * W) * 3,
+                     2 * W * 4, &full[s]);
+            bulk_g2s(st + kStateB + kCovB + kHitB + b * 6 * W * 4, a.hitcov + (first + b * W) * 6,
+                     3 * W * 4, &full[s]);
+          }
+        }
         issued = k + 1;
       }
       // No copy may still be writing this CTA's shared memory when it exits
