@@ -55,7 +55,9 @@ NOMINAL_HBM_GBS = 7900.0
 KERNEL_SOURCES = ("paper_2401_14221_gb300/csrc/kf_common.cuh",
                   "paper_2401_14221_gb300/csrc/kf_device.cuh",
                   "paper_2401_14221_gb300/csrc/kf_step.cuh",
-                  "paper_2401_14221_gb300/csrc/kf_step_staged.cu")
+                  "paper_2401_14221_gb300/csrc/kf_step_staged.cuh",
+                  "paper_2401_14221_gb300/csrc/kf_step_staged.cu",
+                  "paper_2401_14221_gb300/csrc/kf_staged_p2r_f32.cu")
 
 
 def parse():
@@ -575,8 +577,8 @@ def main():
         torch.cuda.synchronize()
         return a.elapsed_time(b_) / (replays * len(batches))
 
-    # Kernel x layout sweep (outside the timed region): the direct kernel on
-    # SoA and AoSoA, the staged kernel on AoSoA block widths.
+    # Kernel x layout sweep (outside the timed region): the direct kernel and
+    # the staged kernel (2 or 3 CTAs per SM) on SoA and the AoSoA widths.
     modes = {"direct": kf.KF_STEP_DIRECT, "staged": kf.KF_STEP_STAGED,
              "staged2": kf.KF_STEP_STAGED, "staged3": kf.KF_STEP_STAGED}
     sweep = {}
@@ -586,8 +588,6 @@ def main():
                 continue
             bs = [kf.upload(w, kind, width, dev) for _ in range(2)]
             for mname, mode in modes.items():
-                if kind == kf.KF_SOA and mname.startswith("staged"):
-                    continue
                 if args.step_kernel != "auto" and mname != args.step_kernel:
                     continue
                 kf.kf_set_step_kernel(mode)

@@ -329,7 +329,8 @@ int kf_propagate_update_host_noalloc(int32_t kind, const kf_params *params,
  * n bucket = floor(log2 n)); later calls in KF_STEP_AUTO mode use it.  No
  * paper counterpart (the paper fixes bsize and launch shapes by hand).
  * Single-step candidates: one thread per track with 128 or 256 threads per
- * CTA; for AoSoA also the persistent staged kernel with 1, 2 or 3 CTAs per
+ * CTA; for AoSoA (and SoA with n a multiple of 4) also the persistent staged
+ * kernel with 1, 2 or 3 CTAs per
  * SM (3: two pipeline stages per CTA instead of three, FP32-arithmetic
  * variants only; the others run it as 2).
  * Chain candidates: 64, 128 or 256 threads per CTA.
@@ -462,12 +463,13 @@ int kf_server_destroy(kf_server *s);
 /*
  * kf_set_step_kernel -- choose the single-step kernel for all later calls in
  * this process (a tuning knob; the results are the same, bit for bit):
- *   KF_STEP_AUTO    (default) the staged kernel for AoSoA layouts, the direct
- *                   kernel for SoA;
+ *   KF_STEP_AUTO    (default) the autotuner's choice where it has one, else
+ *                   the staged kernel where it applies, else the direct one;
  *   KF_STEP_DIRECT  one thread per track with direct global loads (any layout);
- *   KF_STEP_STAGED  a persistent kernel in which a producer warp streams AoSoA
+ *   KF_STEP_STAGED  a persistent kernel in which a producer warp streams
  *                   tiles into shared memory with bulk asynchronous copies
- *                   while eight warps compute (SoA falls back to direct).
+ *                   while eight warps compute: any AoSoA layout, and SoA when
+ *                   n is a multiple of 4 (otherwise the direct kernel runs).
  * Returns KF_ERR_ARG for an unknown mode.
  */
 #define KF_STEP_AUTO   0

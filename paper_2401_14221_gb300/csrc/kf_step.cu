@@ -168,7 +168,10 @@ int launch_step_kernel(int kind, int precision, const StepArgs &a, cudaStream_t 
 }
 
 static int launch_step_main(int kind, int precision, const StepArgs &a, cudaStream_t s) {
-  LaunchConfig cfg{a.soa ? KF_STEP_DIRECT : KF_STEP_STAGED, 256, 2};
+  // The staged kernel copies whole tiles with 16-byte-aligned bulk copies:
+  // any AoSoA layout, SoA when n is a multiple of 4.
+  const bool staged_ok = !a.soa || (a.n & 3) == 0;
+  LaunchConfig cfg{staged_ok ? KF_STEP_STAGED : KF_STEP_DIRECT, 256, 2};
   if (const LaunchConfig *o = thread_override()) {
     cfg = *o;
   } else {
@@ -176,6 +179,7 @@ static int launch_step_main(int kind, int precision, const StepArgs &a, cudaStre
     if (mode == KF_STEP_DIRECT) {
       cfg.kernel = KF_STEP_DIRECT;
     } else if (mode == KF_STEP_STAGED) {
+      cfg.kernel = KF_STEP_STAGED;
       const int c = g_staged_ctas.load(std::memory_order_relaxed);
       if (c > 0) cfg.ctas_per_sm = c;
     } else if (mode == KF_STEP_AUTO) {
@@ -183,8 +187,7 @@ static int launch_step_main(int kind, int precision, const StepArgs &a, cudaStre
       if (tune_lookup(kOpStep, kind, precision, a.soa, a.lw, a.n, &t)) cfg = t;
     }
   }
-  // AoSoA tiles are contiguous runs: stage them with bulk copies.
-  if (!a.soa && cfg.kernel == KF_STEP_STAGED)
+  if (staged_ok && cfg.kernel == KF_STEP_STAGED)
     return launch_step_staged(kind, precision, a, s, cfg.ctas_per_sm);
   const int threads = (cfg.threads == 128 || cfg.threads == 64) ? cfg.threads : 256;
   const int64_t blocks = (a.n + threads - 1) / threads;

@@ -25,6 +25,7 @@ struct StepArgs {
   int32_t lw;
   float bz;
   int32_t surf_per_track;
+  unsigned *err = nullptr;  // device error word (set by the staged launcher)
 };
 
 #ifdef __CUDACC__

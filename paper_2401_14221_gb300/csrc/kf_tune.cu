@@ -137,7 +137,7 @@ extern "C" int kf_autotune_step(int32_t kind, const kf_params *params, kf_layout
                            {KF_STEP_STAGED, 256, 1},
                            {KF_STEP_STAGED, 256, 2},
                            {KF_STEP_STAGED, 256, 3}};
-  const int ncand = d.soa ? 2 : 5;
+  const int ncand = (d.soa && (d.n & 3)) ? 2 : 5;  // staged: AoSoA, or SoA with n % 4 == 0
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   // Candidates take turns over kRounds rounds (so that clock or memory
   // drift during tuning hits all of them alike); each keeps its median.
