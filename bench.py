@@ -78,7 +78,8 @@ def parse():
     ap.add_argument("--chain-steps", type=int, default=10)
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--no-scaling", action="store_true",
-                    help="skip the 240k / 3.84M batch-size context measurement")
+                    help="skip the context measurements of other sizes (240k / 3.84M p2r, "
+                         "8,192 and 960k p2z)")
     ap.add_argument("--no-serving", action="store_true",
                     help="skip the serving-loop measurement")
     ap.add_argument("--serve-events", type=int, default=2048)
@@ -665,12 +666,12 @@ def main():
     # of one launch, graph-replayed back to back; and p2z at the p2r batch
     # size (237 algorithmic bytes per track: hit z and three hit-covariance
     # entries are not read)
-    w_small = W.make_p2z(8192, seed=shard.rank_seed(1, rank))
-    small = [kf.upload(w_small, kind, width, dev) for _ in range(2)]
-    p2z_small_us = graph_time(small, 500) * 1e3
-    del small
-    p2z_big = None
+    p2z_small_us, p2z_big = None, None
     if not args.no_scaling:
+        w_small = W.make_p2z(8192, seed=shard.rank_seed(1, rank))
+        small = [kf.upload(w_small, kind, width, dev) for _ in range(2)]
+        p2z_small_us = graph_time(small, 500) * 1e3
+        del small
         w_z = W.make_p2z(w.n, seed=shard.rank_seed(2, rank))
         bz_ = [kf.upload(w_z, kind, width, dev) for _ in range(4)]
         ms_z = graph_time(bz_, 200)

@@ -86,6 +86,9 @@ template <int KIND>
 __global__ void __launch_bounds__(256) redo_pass_kernel(const __grid_constant__ StepArgs a) {
   __shared__ int32_t list[kRedoSpan];
   __shared__ int count;
+  // launched as a programmatic dependent of the step kernel: wait here until
+  // it has completed and its status marks are visible
+  asm volatile("griddepcontrol.wait;" ::: "memory");
   const int64_t span0 = (int64_t)blockIdx.x * kRedoSpan;
   const int cnt = gather_marked(a.status, span0, a.n, list, &count);
   for (int q = threadIdx.x; q < cnt; q += blockDim.x) {
@@ -99,11 +102,19 @@ int launch_redo_pass(int kind, const StepArgs &a, cudaStream_t s) {
   const int64_t blocks = (a.n + kRedoSpan - 1) / kRedoSpan;
   if (blocks > 0x7fffffffLL) return set_error(KF_ERR_ARG, "n too large for one launch");
   const unsigned g = (unsigned)blocks;
-  if (kind == kP2z)
-    redo_pass_kernel<kP2z><<<g, 256, 0, s>>>(a);
-  else
-    redo_pass_kernel<kP2r><<<g, 256, 0, s>>>(a);
-  return check_cuda(cudaGetLastError(), "adaptive redo pass launch");
+  // programmatic dependent launch: scheduled while the step kernel drains
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(g);
+  cfg.blockDim = dim3(256);
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  const cudaError_t e = kind == kP2z ? cudaLaunchKernelEx(&cfg, redo_pass_kernel<kP2z>, a)
+                                     : cudaLaunchKernelEx(&cfg, redo_pass_kernel<kP2r>, a);
+  return check_cuda(e, "adaptive redo pass launch");
 }
 
 template <int KIND>

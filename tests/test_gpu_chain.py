@@ -6,6 +6,7 @@ import pytest
 import torch
 
 import oracle
+import parity_log
 from oracle import compare
 from paper_2401_14221_gb300 import build as kbuild
 from paper_2401_14221_gb300 import kf
@@ -146,6 +147,7 @@ def test_chain_matches_oracle_on_256_events(dev, chain_full, chain_sample, preci
     o_st, o_cv, o_stat = oracle_chain(cw, idx, VARIANT_FORM[precision])
     rep = compare.compare(st.T[idx], cv.T[idx], stat[idx], o_st, o_cv, o_stat,
                           on_cylinder=ends_on_cylinder(cw, o_st))
+    parity_log.record("chain", rep)
     assert rep["ok"], rep
 
 
@@ -187,6 +189,7 @@ def test_adaptive_chain_redo_pass(dev, chain_full):
     o_st, o_cv, o_stat = oracle_chain(cw, idx, oracle.FORM_STANDARD)
     rep = compare.compare(ada[0].T[idx], ada[1].T[idx], ada[2][idx], o_st, o_cv, o_stat,
                           on_cylinder=ends_on_cylinder(cw, o_st))
+    parity_log.record("chain", rep)
     assert rep["ok"], {k: rep.get(k) for k in ("param", "cov", "worst_param", "worst_cov")}
     # the status array is required
     with pytest.raises(kf.KfError) as e:

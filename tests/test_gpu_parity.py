@@ -13,6 +13,7 @@ import pytest
 import torch
 
 import oracle
+import parity_log
 from oracle import compare
 from paper_2401_14221_gb300 import build as kbuild
 from paper_2401_14221_gb300 import kf
@@ -91,6 +92,7 @@ def check(w, b, idx, form=oracle.FORM_STANDARD, surf=None):
     o_st, o_cv, o_stat, _ = oracle_on(w, idx, form, surf)
     rep = compare.compare(st.T[idx], cv.T[idx], stat[idx], o_st, o_cv, o_stat,
                           on_cylinder=cylinder_frame(w, o_stat))
+    parity_log.record("step", rep)
     assert rep["ok"], {k: rep.get(k) for k in ("n", "param", "cov", "status_mismatch",
                                                "worst_param", "worst_cov")}
     return rep
@@ -193,6 +195,7 @@ def test_per_track_surfaces(dev, step_kernel, precision):
     o_st, o_cv, o_stat, _ = oracle_on(w, np.arange(w.n))
     on_cyl = (o_stat & oracle.NO_INTERSECT) == 0
     rep = compare.compare(st.T, cv.T, stat, o_st, o_cv, o_stat, on_cylinder=on_cyl)
+    parity_log.record("step", rep)
     assert rep["ok"], rep
     assert rep["flagged"] > 0 and rep["flagged"] == int(np.sum(~w.reached))
 
@@ -305,6 +308,7 @@ def test_offsets_beyond_2_to_31_elements(dev):
     o_st, o_cv, o_stat, _ = oracle_on(base, bi)
     rep = compare.compare(g_st, g_cv, g_stat, o_st, o_cv, o_stat,
                           on_cylinder=cylinder_frame(base, o_stat))
+    parity_log.record("step", rep)
     assert rep["ok"], rep
     del st_in, cv_in, st_out, cv_out
     torch.cuda.empty_cache()
@@ -369,6 +373,7 @@ def test_host_array_entry_matches_device_entry(dev, layout, pinned):
         o_st, o_cv, o_stat, _ = oracle_on(w, idx)
         rep = compare.compare(got[0].T[idx], got[1].T[idx], got[2][idx], o_st, o_cv, o_stat,
                               on_cylinder=cylinder_frame(w, o_stat))
+        parity_log.record("step", rep)
         assert rep["ok"], rep
 
 
@@ -456,6 +461,7 @@ def test_compressed_covariance_step(dev, w_prec, layout):
                                                   w.surf, w.bz, threads=8)
         rep = compare.compare(g_st.T[idx], g_cov.T[idx], status.cpu().numpy()[idx], o_st, o_cv,
                               o_stat, on_cylinder=cylinder_frame(w, o_stat))
+        parity_log.record("step", rep)
         assert rep["ok"], rep
 
 
@@ -507,4 +513,5 @@ def test_compressed_adaptive_redo_pass(dev):
                                               w.hitcov.T, w.surf, w.bz, threads=8)
     on_cyl = (o_stat & oracle.NO_INTERSECT) == 0
     rep = compare.compare(g[0].T, g[1].T, g[2], o_st, o_cv, o_stat, on_cylinder=on_cyl)
+    parity_log.record("step", rep)
     assert rep["ok"], rep

@@ -14,6 +14,7 @@ import pytest
 import torch
 
 import oracle
+import parity_log
 from oracle import compare
 from paper_2401_14221_gb300 import build as kbuild
 from paper_2401_14221_gb300 import kf
@@ -135,6 +136,7 @@ def test_server_results_match_the_oracle(dev, events, precision):
                 on_cyl |= np.abs(r - R) <= 1e-5 * R
             rep = compare.compare(outs[0].numpy().T, outs[1].numpy().T, outs[2].numpy(), o_st,
                                   o_cv, o_stat, on_cylinder=on_cyl & ~on_plane)
+            parity_log.record("server", rep)
             assert rep["ok"], rep
     finally:
         srv.close()
