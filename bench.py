@@ -443,7 +443,8 @@ def serving_bench(args, kf, W, dev, rank):
                           "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"], "max_ms": st["max_ms"],
                           "batches": st["batches"], "max_batch_events": st["max_batch_events"],
                           "phases_ms": {ph: [st[f"{ph}_p50_ms"], st[f"{ph}_p99_ms"]]
-                                        for ph in ("queue", "ready", "compute", "out")}}
+                                        for ph in ("queue", "ready", "copyin", "compute",
+                                                   "out")}}
 
     runs = [serve(rate, 12 + rank + k) for k, rate in enumerate(args.serve_rates)]
     srv.close()

@@ -420,6 +420,9 @@ typedef struct {
      * out = copy-out issued -> landed in host memory. */
     double  queue_p50_ms, queue_p99_ms, ready_p50_ms, ready_p99_ms;
     double  compute_p50_ms, compute_p99_ms, out_p50_ms, out_p99_ms;
+    /* the copy-in part of 'ready': admitted -> its copies seen landed (the
+     * rest of 'ready' is waiting for the batch in flight to finish) */
+    double  copyin_p50_ms, copyin_p99_ms;
 } kf_server_stats;
 
 /* Arena bytes one event of n tracks and L layers occupies (-1 if invalid). */

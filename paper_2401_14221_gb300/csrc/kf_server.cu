@@ -200,7 +200,8 @@ struct Request {
   int64_t off = -1;  // arena offset
   Layout lay{};
   cudaEvent_t ev = nullptr;  // copies in / copies out landed
-  std::chrono::steady_clock::time_point t_submit, t_admit, t_launch, t_finished, t_done;
+  std::chrono::steady_clock::time_point t_submit, t_admit, t_copied, t_launch, t_finished, t_done;
+  bool copied = false;  // copy-in seen complete (t_copied set)
 };
 
 // First-fit allocator over [0, size) with coalescing.
@@ -260,7 +261,7 @@ struct kf_server {
   int in_flight = 0;  // admitted, not yet done
   // statistics
   std::vector<double> latencies_ms;
-  std::vector<double> phase_ms[4];  // queue, ready, compute, out
+  std::vector<double> phase_ms[5];  // queue, ready, compute, out, copy-in
   int64_t tracks_done = 0, batches = 0, max_batch_events = 0;
 };
 
@@ -395,6 +396,7 @@ bool schedule_once(kf_server *s) {
     s->phase_ms[1].push_back(ms(r->t_admit, r->t_launch));
     s->phase_ms[2].push_back(ms(r->t_launch, r->t_finished));
     s->phase_ms[3].push_back(ms(r->t_finished, r->t_done));
+    s->phase_ms[4].push_back(ms(r->t_admit, r->t_copied));
     s->tracks_done += r->n;
     s->arena.release(r->off, r->lay.bytes);
     s->event_pool.push_back(r->ev);
@@ -440,12 +442,22 @@ bool schedule_once(kf_server *s) {
     s->copying.push_back(r);
     moved = true;
   }
+  // note when copies land (the copy-in phase ends even while a batch runs)
+  {
+    const auto now = std::chrono::steady_clock::now();
+    for (Request *r : s->copying) {
+      if (!r->copied && cudaEventQuery(r->ev) == cudaSuccess) {
+        r->copied = true;
+        r->t_copied = now;
+      }
+    }
+  }
   // launch everything whose copies have landed
   if (!s->batch_in_flight && !s->copying.empty()) {
     std::vector<Request *> batch;
     for (size_t k = 0; k < s->copying.size() && (int)batch.size() < kf::srv::kMaxBatch;) {
       Request *r = s->copying[k];
-      if (cudaEventQuery(r->ev) == cudaSuccess) {
+      if (r->copied) {
         batch.push_back(r);
         s->copying.erase(s->copying.begin() + k);
       } else {
@@ -648,11 +660,12 @@ extern "C" int kf_server_get_stats(kf_server *s, kf_server_stats *out) {
     for (double x : v) sum += x;
     out->mean_ms = sum / (double)v.size();
   }
-  double *dst[4][2] = {{&out->queue_p50_ms, &out->queue_p99_ms},
+  double *dst[5][2] = {{&out->queue_p50_ms, &out->queue_p99_ms},
                        {&out->ready_p50_ms, &out->ready_p99_ms},
                        {&out->compute_p50_ms, &out->compute_p99_ms},
-                       {&out->out_p50_ms, &out->out_p99_ms}};
-  for (int k = 0; k < 4; ++k) {
+                       {&out->out_p50_ms, &out->out_p99_ms},
+                       {&out->copyin_p50_ms, &out->copyin_p99_ms}};
+  for (int k = 0; k < 5; ++k) {
     std::vector<double> w = s->phase_ms[k];
     if (w.empty()) continue;
     std::sort(w.begin(), w.end());

@@ -69,7 +69,8 @@ class kf_server_stats(ctypes.Structure):
                 ("queue_p50_ms", ctypes.c_double), ("queue_p99_ms", ctypes.c_double),
                 ("ready_p50_ms", ctypes.c_double), ("ready_p99_ms", ctypes.c_double),
                 ("compute_p50_ms", ctypes.c_double), ("compute_p99_ms", ctypes.c_double),
-                ("out_p50_ms", ctypes.c_double), ("out_p99_ms", ctypes.c_double)]
+                ("out_p50_ms", ctypes.c_double), ("out_p99_ms", ctypes.c_double),
+                ("copyin_p50_ms", ctypes.c_double), ("copyin_p99_ms", ctypes.c_double)]
 
 
 _lib = None

@@ -179,8 +179,9 @@ def test_paused_server_wait_times_out_then_completes(dev, events):
         # the latency split: the event sat in the queue for the whole pause
         st = srv.stats()
         assert st["events_done"] == 1 and st["queue_p50_ms"] >= 50.0
-        for ph in ("queue", "ready", "compute", "out"):
+        for ph in ("queue", "ready", "copyin", "compute", "out"):
             assert 0.0 <= st[f"{ph}_p50_ms"] <= st[f"{ph}_p99_ms"]
+        assert st["copyin_p50_ms"] <= st["ready_p50_ms"]  # copy-in is part of ready
         assert st["queue_p50_ms"] + st["ready_p50_ms"] + st["compute_p50_ms"] + \
             st["out_p50_ms"] <= st["max_ms"] + 1e-6
     finally:
