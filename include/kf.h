@@ -88,7 +88,9 @@ typedef struct {
 #define KF_FP32           0 /* all arithmetic in FP32                       */
 #define KF_FP64_UPDATE    1 /* FP32 propagation; S^-1, K and C'' in FP64     */
 #define KF_JOSEPH         2 /* FP32, Joseph-form C'' = (I-KH)C'(I-KH)^T+KVK^T */
-#define KF_FP64           3 /* every operation of the step in FP64           */
+#define KF_FP64           3 /* every operation of the step in FP64 (in the
+                               chain the state also stays in FP64 between
+                               layers)                                       */
 #define KF_ADAPTIVE       4 /* FP32, and the whole step redone in FP64 for a
                                track whose FP32 step is ill-conditioned: the
                                hit shrinks a measured variance by more than
@@ -97,7 +99,9 @@ typedef struct {
                                C' - K H C' loses more digits than FP32 holds
                                (the propagated covariance is rounded element
                                by element, which breaks the near-perfect
-                               correlations the update divides out).  Other
+                               correlations the update divides out).  In the
+                               chain such a track reruns the whole chain with
+                               its state in FP64.  Other
                                tracks run at the FP32 cost.  The single-step
                                entry points on device arrays (and the
                                compressed one) and the chain need a status
