@@ -50,14 +50,15 @@ FLOPS_PER_TRACK_LAYER = 465
 FP32_LANES = 152 * 128
 FALLBACK_HBM_GBS = 6800.0
 NOMINAL_HBM_GBS = 7900.0
-# what the staged step kernel is compiled from (the capture in profiles/ is
-# valid while these are unchanged)
+# what the staged step kernel is compiled from, flags included (the capture
+# in profiles/ is valid while these are unchanged)
 KERNEL_SOURCES = ("paper_2401_14221_gb300/csrc/kf_common.cuh",
                   "paper_2401_14221_gb300/csrc/kf_device.cuh",
                   "paper_2401_14221_gb300/csrc/kf_step.cuh",
                   "paper_2401_14221_gb300/csrc/kf_step_staged.cuh",
                   "paper_2401_14221_gb300/csrc/kf_step_staged.cu",
-                  "paper_2401_14221_gb300/csrc/kf_staged_p2r_f32.cu")
+                  "paper_2401_14221_gb300/csrc/kf_staged_p2r_f32.cu",
+                  "paper_2401_14221_gb300/build.py")
 
 
 def parse():
