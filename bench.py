@@ -294,7 +294,8 @@ def compressed_bench(kf, W, w, dev, kind, width):
     torch.cuda.synchronize()
     ms = a.elapsed_time(e) / 100
     return {"ms": ms, "tracks_per_s": w.n / (ms * 1e-3), "bytes_per_track": 193,
-            "GBps": 193 * w.n / (ms * 1e-3) / 1e9, "kernel": "direct (one thread per track)"}
+            "GBps": 193 * w.n / (ms * 1e-3) / 1e9,
+            "kernel": "staged (bulk copies)" if kind == kf.KF_AOSOA else "one thread per track"}
 
 
 def chain_bench(args, kf, W, dev, rank):

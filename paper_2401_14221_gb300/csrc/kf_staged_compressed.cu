@@ -1,0 +1,225 @@
+// kf_staged_compressed.cu -- the single step on the compressed covariance
+// store (FP32 sigmas, FP16 correlations), staged like the FP32-store step:
+// a persistent CTA whose producer warp streams AoSoA tiles of 256 tracks into
+// shared memory with bulk asynchronous copies (state, sigma, rho, hit, hit
+// covariance: five contiguous runs per tile) while eight compute warps
+// decode, step, encode and store.  The one-thread-per-track kernel reads 193
+// algorithmic bytes per p2r track through 2- and 4-byte loads; staging moves
+// them at the bulk-copy rate.  Arithmetic and results are those of the
+// one-thread-per-track kernel, bit for bit.
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+
+#include <atomic>
+
+#include "kf_compressed.cuh"
+#include "kf_step_staged.cuh"
+
+namespace kf {
+namespace staged {
+// defined with the staged step kernel's dispatch (kf_step_staged.cu)
+int sm_count(int dev, int *out);
+int error_word(int dev, unsigned **out);
+}  // namespace staged
+
+namespace {
+
+using staged::bulk_g2s;
+using staged::kComputeWarps;
+using staged::kT;
+using staged::kThreads;
+using staged::mbar_arrive;
+using staged::mbar_arrive_expect_tx;
+using staged::mbar_fence_init;
+using staged::mbar_init;
+using staged::mbar_wait;
+using staged::Schedule;
+
+constexpr int kStateB = kT * 6 * 4;
+constexpr int kSigB = kT * 6 * 4;
+constexpr int kRhoB = kT * 15 * 2;
+constexpr int kHitB = kT * 3 * 4;
+constexpr int kHcB = kT * 6 * 4;
+constexpr int kStageB = kStateB + kSigB + kRhoB + kHitB + kHcB;  // 29,184 B
+constexpr int kStages = 3;
+constexpr int kSmem = kStages * (kStageB + 16);
+
+template <int KIND, int VARIANT, int W>
+__global__ void __launch_bounds__(kThreads, 2)
+    compressed_staged_kernel(const __grid_constant__ CompressedArgs a, unsigned *err) {
+  static_assert(kT % W == 0, "tile must hold whole AoSoA blocks");
+  extern __shared__ __align__(128) unsigned char smem[];
+  uint64_t *full = reinterpret_cast<uint64_t *>(smem + kStages * kStageB);
+  uint64_t *empty = full + kStages;
+  const int warp = threadIdx.x >> 5;
+  const int lane = threadIdx.x & 31;
+  const Schedule sch = staged::make_schedule<W>(a.n, gridDim.x);
+  const int64_t ntiles = sch.tiles_of(blockIdx.x);
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kStages; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], kComputeWarps);
+    }
+    mbar_fence_init();
+  }
+  __syncthreads();
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+
+  if (warp == kComputeWarps) {
+    // ------------------------------------------------------------ producer
+    if (lane == 0) {
+      int64_t issued = 0;
+      for (int64_t k = 0; k < ntiles; ++k) {
+        const int s = (int)(k % kStages);
+        const uint32_t ph = (uint32_t)(k / kStages) & 1u;
+        if (k >= kStages && !mbar_wait(&empty[s], ph ^ 1u, err)) break;
+        int64_t first, m;
+        sch.tile(k, blockIdx.x, a.n, &first, &m);
+        const uint32_t cols = (uint32_t)(((m + W - 1) / W) * W);  // whole blocks
+        unsigned char *st = smem + s * kStageB;
+        mbar_arrive_expect_tx(&full[s], cols * (6 * 4 + 6 * 4 + 15 * 2 + 3 * 4 + 6 * 4));
+        bulk_g2s(st, a.state_in + first * 6, cols * 6 * 4, &full[s]);
+        bulk_g2s(st + kStateB, a.sigma_in + first * 6, cols * 6 * 4, &full[s]);
+        bulk_g2s(st + kStateB + kSigB, a.rho_in + first * 15, cols * 15 * 2, &full[s]);
+        bulk_g2s(st + kStateB + kSigB + kRhoB, a.hit + first * 3, cols * 3 * 4, &full[s]);
+        bulk_g2s(st + kStateB + kSigB + kRhoB + kHitB, a.hitcov + first * 6, cols * 6 * 4,
+                 &full[s]);
+        issued = k + 1;
+      }
+      for (int64_t k = issued > kStages ? issued - kStages : 0; k < issued; ++k)
+        if (!mbar_wait(&full[k % kStages], (uint32_t)(k / kStages) & 1u, err)) break;
+    }
+    return;
+  }
+
+  // --------------------------------------------------------------- compute
+  const int il = warp * 32 + lane;
+  const int blk = il / W, r = il % W;
+  for (int64_t k = 0; k < ntiles; ++k) {
+    const int s = (int)(k % kStages);
+    const uint32_t ph = (uint32_t)(k / kStages) & 1u;
+    int64_t first, m;
+    sch.tile(k, blockIdx.x, a.n, &first, &m);
+    const int64_t i = first + il;
+    const bool live = il < m;
+    const float qf = live ? (float)__ldg(a.charge + i) : 1.0f;
+    const float surf = __ldg(a.surf + ((a.surf_per_track && live) ? i : 0));
+    if (!mbar_wait(&full[s], ph, err)) break;
+
+    const unsigned char *st = smem + s * kStageB;
+    const float *sst = reinterpret_cast<const float *>(st);
+    const float *ssg = reinterpret_cast<const float *>(st + kStateB);
+    const __half *srh = reinterpret_cast<const __half *>(st + kStateB + kSigB);
+    const float *sht = reinterpret_cast<const float *>(st + kStateB + kSigB + kRhoB);
+    const float *shc = reinterpret_cast<const float *>(st + kStateB + kSigB + kRhoB + kHitB);
+    float p[6], sg[6], hc[6];
+    __half rh[15];
+#pragma unroll
+    for (int c = 0; c < 6; ++c) p[c] = sst[blk * 6 * W + c * W + r];
+#pragma unroll
+    for (int c = 0; c < 6; ++c) sg[c] = ssg[blk * 6 * W + c * W + r];
+#pragma unroll
+    for (int q = 0; q < 15; ++q) rh[q] = srh[blk * 15 * W + q * W + r];
+    const float hx = sht[blk * 3 * W + r];
+    const float hy = sht[blk * 3 * W + W + r];
+    const float hz = sht[blk * 3 * W + 2 * W + r];
+#pragma unroll
+    for (int c = 0; c < 6; ++c) hc[c] = shc[blk * 6 * W + c * W + r];
+    __syncwarp();
+    if (lane == 0) mbar_arrive(&empty[s]);  // stage may be refilled
+    if (!live) continue;
+
+    float C[21];
+    decode_cov(sg, rh, C);
+    unsigned stt;
+    if (KIND == kP2z)
+      stt = p2z_step<VARIANT>(p, C, qf, a.bz, surf, hx, hy, hc[0], hc[1], hc[2]);
+    else
+      stt = p2r_step<VARIANT>(p, C, qf, a.bz, surf, hx, hy, hz, hc);
+    if constexpr (VARIANT == kAdaptive) {
+      if (stt & kRedo) {  // left to the FP64 redo pass, inputs untouched
+        a.status[i] = (uint8_t)kRedo;
+        continue;
+      }
+    }
+    stt |= finite_status(p, C);
+    if (!(stt & kNoIntersect)) encode_cov(C, sg, rh);  // else: the input sigma / rho
+    const int64_t b6 = (i / W) * (6 * W) + (i % W);
+    const int64_t b15 = (i / W) * (15 * W) + (i % W);
+#pragma unroll
+    for (int c = 0; c < 6; ++c) __stcs(a.state_out + b6 + c * W, p[c]);
+#pragma unroll
+    for (int c = 0; c < 6; ++c) __stcs(a.sigma_out + b6 + c * W, sg[c]);
+#pragma unroll
+    for (int q = 0; q < 15; ++q) a.rho_out[b15 + q * W] = rh[q];
+    if (a.status) a.status[i] = (uint8_t)stt;
+  }
+}
+
+template <int KIND, int VARIANT, int W>
+int launch_w(const CompressedArgs &a, cudaStream_t s, int grid, unsigned *err, int dev) {
+  auto kern = compressed_staged_kernel<KIND, VARIANT, W>;
+  static std::atomic<bool> configured[64] = {};
+  if (dev < 0 || dev >= 64 || !configured[dev].load(std::memory_order_acquire)) {
+    if (int rc = check_cuda(
+            cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem),
+            "cudaFuncSetAttribute"))
+      return rc;
+    if (dev >= 0 && dev < 64) configured[dev].store(true, std::memory_order_release);
+  }
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)grid);
+  cfg.blockDim = dim3(kThreads);
+  cfg.dynamicSmemBytes = kSmem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return check_cuda(cudaLaunchKernelEx(&cfg, kern, a, err), "compressed staged launch");
+}
+
+template <int KIND, int VARIANT>
+int launch_v(const CompressedArgs &a, cudaStream_t s, int grid, unsigned *err, int dev) {
+  switch (a.lw) {
+    case 4: return launch_w<KIND, VARIANT, 16>(a, s, grid, err, dev);
+    case 5: return launch_w<KIND, VARIANT, 32>(a, s, grid, err, dev);
+    case 6: return launch_w<KIND, VARIANT, 64>(a, s, grid, err, dev);
+    default: return launch_w<KIND, VARIANT, 128>(a, s, grid, err, dev);
+  }
+}
+
+}  // namespace
+
+int launch_compressed_staged(int kind, int precision, const CompressedArgs &a, cudaStream_t s) {
+  if (a.n == 0) return KF_OK;
+  if (a.soa) return set_error(KF_ERR_UNSUPPORTED, "the staged compressed step takes AoSoA");
+  int dev = 0, sms = 0;
+  if (int rc = check_cuda(cudaGetDevice(&dev), "cudaGetDevice")) return rc;
+  if (int rc = staged::sm_count(dev, &sms)) return rc;
+  unsigned *err = nullptr;
+  if (int rc = staged::error_word(dev, &err)) return rc;
+  const int64_t ntiles = (a.n + kT - 1) / kT;
+  const int64_t slots = 2LL * sms;
+  const int grid = (int)(ntiles < slots ? ntiles : slots);
+  // the float-arithmetic variants (the FP64 ones stay one thread per track)
+  if (kind == kP2z) {
+    switch (precision) {
+      case KF_FP32: return launch_v<kP2z, kFP32>(a, s, grid, err, dev);
+      case KF_JOSEPH: return launch_v<kP2z, kJoseph>(a, s, grid, err, dev);
+      case KF_ADAPTIVE: return launch_v<kP2z, kAdaptive>(a, s, grid, err, dev);
+      default: return set_error(KF_ERR_UNSUPPORTED, "staged compressed: FP32 variants only");
+    }
+  }
+  switch (precision) {
+    case KF_FP32: return launch_v<kP2r, kFP32>(a, s, grid, err, dev);
+    case KF_JOSEPH: return launch_v<kP2r, kJoseph>(a, s, grid, err, dev);
+    case KF_ADAPTIVE: return launch_v<kP2r, kAdaptive>(a, s, grid, err, dev);
+    default: return set_error(KF_ERR_UNSUPPORTED, "staged compressed: FP32 variants only");
+  }
+}
+
+}  // namespace kf

@@ -15,30 +15,12 @@
 #include <cuda_runtime.h>
 
 #include "kf_common.cuh"
+#include "kf_compressed.cuh"
 #include "kf_device.cuh"
 #include "kf_step.cuh"
 
 namespace kf {
 namespace {
-
-struct CompressedArgs {
-  const float *state_in;
-  const float *sigma_in;
-  const __half *rho_in;
-  float *state_out;
-  float *sigma_out;
-  __half *rho_out;
-  const int8_t *charge;
-  const float *hit;
-  const float *hitcov;
-  const float *surf;
-  uint8_t *status;
-  int64_t n;
-  int32_t soa;
-  int32_t lw;
-  float bz;
-  int32_t surf_per_track;
-};
 
 struct Loc {
   int64_t base;
@@ -52,30 +34,21 @@ __device__ __forceinline__ Loc locate(int64_t i, int64_t n, int32_t soa, int32_t
   return {(i >> lw) * (C * W) + (i & (W - 1)), W};
 }
 
-// Off-diagonal (row, column) of correlation k, packed order.
-__device__ __forceinline__ constexpr int od_row(int k) {
-  return k < 1 ? 1 : k < 3 ? 2 : k < 6 ? 3 : k < 10 ? 4 : 5;
-}
-__device__ __forceinline__ constexpr int od_col(int k) {
-  return k - (od_row(k) * (od_row(k) - 1)) / 2;
-}
-
-// Load track i: state, and the covariance decoded from sigma / rho
-// (C_ii = sigma_i^2, C_ij = rho_ij sigma_i sigma_j).
+// Load track i: state, and the covariance decoded from sigma / rho.
 template <class T>
 __device__ __forceinline__ void load_compressed(const CompressedArgs &a, const Loc &l6,
                                                 const Loc &l15, T (&p)[6], T (&C)[21]) {
-  float sg[6];
+  float sg[6], Cf[21];
+  __half rh[15];
 #pragma unroll
   for (int c = 0; c < 6; ++c) p[c] = __ldg(a.state_in + l6.base + c * l6.stride);
 #pragma unroll
   for (int c = 0; c < 6; ++c) sg[c] = __ldg(a.sigma_in + l6.base + c * l6.stride);
 #pragma unroll
-  for (int c = 0; c < 6; ++c) C[tri(c, c)] = T(sg[c] * sg[c]);
+  for (int k = 0; k < 15; ++k) rh[k] = a.rho_in[l15.base + k * l15.stride];
+  decode_cov(sg, rh, Cf);
 #pragma unroll
-  for (int k = 0; k < 15; ++k)
-    C[tri(od_row(k), od_col(k))] =
-        T(__half2float(a.rho_in[l15.base + k * l15.stride]) * sg[od_row(k)] * sg[od_col(k)]);
+  for (int e = 0; e < 21; ++e) C[e] = T(Cf[e]);
 }
 
 // Encode and store track i's result; a track that was not propagated gets
@@ -86,18 +59,7 @@ __device__ __forceinline__ void store_compressed(const CompressedArgs &a, const 
   float sg[6];
   __half rh[15];
   if (!(st & kNoIntersect)) {
-    // sigma_i = sqrt(C_ii), rho_ij = C_ij / (sigma_i sigma_j) in [-1, 1]
-    float inv[6];
-#pragma unroll
-    for (int c = 0; c < 6; ++c) {
-      sg[c] = sqrtf(fmaxf(C[tri(c, c)], 0.0f));
-      inv[c] = sg[c] > 0.0f ? 1.0f / sg[c] : 0.0f;
-    }
-#pragma unroll
-    for (int k = 0; k < 15; ++k) {
-      const float r = C[tri(od_row(k), od_col(k))] * inv[od_row(k)] * inv[od_col(k)];
-      rh[k] = __float2half_rn(fminf(fmaxf(r, -1.0f), 1.0f));
-    }
+    encode_cov(C, sg, rh);
   } else {
 #pragma unroll
     for (int c = 0; c < 6; ++c) sg[c] = __ldg(a.sigma_in + l6.base + c * l6.stride);
@@ -245,7 +207,13 @@ extern "C" int kf_propagate_update_compressed(
   if (blocks > 0x7fffffffLL) return set_error(KF_ERR_ARG, "n too large for one launch");
   const unsigned g = (unsigned)blocks;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  if (kind == KF_P2Z) {
+  // AoSoA with a float-arithmetic variant: the staged kernel (same results)
+  const bool staged = !d.soa && step_kernel_mode() != KF_STEP_DIRECT &&
+                      (params->precision == KF_FP32 || params->precision == KF_JOSEPH ||
+                       params->precision == KF_ADAPTIVE);
+  if (staged) {
+    if (int rc = launch_compressed_staged(kind, params->precision, a, s)) return rc;
+  } else if (kind == KF_P2Z) {
     switch (params->precision) {
       case KF_FP32: step_compressed_kernel<kP2z, kFP32><<<g, threads, 0, s>>>(a); break;
       case KF_FP64_UPDATE: step_compressed_kernel<kP2z, kFP64Update><<<g, threads, 0, s>>>(a); break;

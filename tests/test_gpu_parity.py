@@ -515,3 +515,21 @@ def test_compressed_adaptive_redo_pass(dev):
     rep = compare.compare(g[0].T, g[1].T, g[2], o_st, o_cv, o_stat, on_cylinder=on_cyl)
     parity_log.record("step", rep)
     assert rep["ok"], rep
+
+
+@pytest.mark.parametrize("precision", [kf.KF_FP32, kf.KF_JOSEPH, kf.KF_ADAPTIVE])
+@pytest.mark.parametrize("kind", [W.P2Z, W.P2R])
+def test_compressed_staged_equals_direct_bitwise(dev, kind, precision):
+    # AoSoA: the staged compressed kernel; KF_STEP_DIRECT forces the one-
+    # thread-per-track one.  Same arithmetic, same bits (ragged n).
+    w = W.make_p2z(30011, seed=71) if kind == W.P2Z else grazing_p2r(seed=72, n=30011)
+    lay = (kf.KF_AOSOA, 64)
+    kf.kf_set_step_kernel(kf.KF_STEP_AUTO)
+    staged = run_compressed(w, dev, lay, precision)
+    kf.kf_set_step_kernel(kf.KF_STEP_DIRECT)
+    try:
+        direct = run_compressed(w, dev, lay, precision)
+    finally:
+        kf.kf_set_step_kernel(kf.KF_STEP_AUTO)
+    for x, y in zip(staged, direct):
+        assert np.array_equal(x, y)
