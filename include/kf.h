@@ -503,7 +503,9 @@ int kf_set_staged_ctas_per_sm(int32_t ctas);
 #define KF_DEVERR_TIMEOUT 1u
 int kf_take_device_error(unsigned int *error_bits);
 
-/* Library version as MAJOR*10000 + MINOR*100 + PATCH. */
+/* Library version as MAJOR*10000 + MINOR*100 + PATCH (0.2.0 = 200; the
+ * minor number grows with every change of a declared struct or function). */
+#define KF_VERSION 200
 int kf_version(void);
 
 /* Message of the last KF_ERR_* returned on the calling thread ("" if none). */

@@ -97,6 +97,6 @@ int check_layout(const kf_layout &layout, LayoutDesc *out) {
 
 }  // namespace kf
 
-extern "C" int kf_version(void) { return 0 * 10000 + 1 * 100 + 0; }
+extern "C" int kf_version(void) { return KF_VERSION; }
 
 extern "C" const char *kf_last_error_string(void) { return kf::g_error; }
