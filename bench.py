@@ -197,8 +197,15 @@ def reference_arm(args, rank, world):
     cores = os.cpu_count() or 1
     state, cov, hit, hc = (np.ascontiguousarray(a.T, dtype=np.float64)
                            for a in (w.state, w.cov, w.hit, w.hitcov))
-    total = 4_000_000
-    per_step = int(min(w.n, max(4096, total // max(1, args.steps + args.warmup))))
+    # size each step's sample so the whole run takes about a minute of
+    # oracle time (one calibration pass of 65,536 tracks first): per-step
+    # samples large enough that thread start-up does not set the rate
+    cal = min(w.n, 65536)
+    t_cal = time.perf_counter()
+    oracle.step_batch(W.P2R, state[:cal], cov[:cal], w.charge[:cal], hit[:cal], hc[:cal],
+                      w.surf, w.bz, threads=cores)
+    rate = cal / max(time.perf_counter() - t_cal, 1e-6)
+    per_step = int(min(w.n, max(4096, rate * 60.0 / max(1, args.steps + args.warmup))))
 
     def step(i):
         lo = (i * per_step) % (w.n - per_step + 1)
