@@ -400,7 +400,9 @@ typedef struct kf_server kf_server;
 
 typedef struct {
     float    bz;                       /* field, T                              */
-    int32_t  precision;                /* KF_FP32 / KF_FP64_UPDATE / KF_JOSEPH  */
+    int32_t  precision;                /* any KF_* precision variant; KF_ADAPTIVE
+                                          redoes the marked tracks of a batch
+                                          in FP64 before the copy-out      */
     int32_t  L;                        /* layers of every event, 1..KF_MAX_LAYERS */
     kf_layer layers[KF_MAX_LAYERS];
     void    *arena;                    /* DEVICE memory owned by the caller,
@@ -449,11 +451,15 @@ int kf_server_submit(kf_server *s, int64_t n, const float *state,
                      const float *hit_covs, float *state_out, float *cov_out,
                      uint8_t *status_out, uint64_t *ticket);
 
-/* *done = 1 once the event's results are in host memory. */
+/* *done = 1 once the event's results are in host memory.  Polling does not
+ * release the ticket. */
 int kf_server_poll(kf_server *s, uint64_t ticket, int32_t *done);
 
 /* Block until the event is done (KF_OK; the ticket is then released) or
- * timeout_s seconds pass (KF_ERR_TIMEOUT; the ticket stays valid). */
+ * timeout_s seconds pass (KF_ERR_TIMEOUT; the ticket stays valid).  A
+ * ticket's record (a few hundred bytes of host memory) is freed only by a
+ * successful wait or by kf_server_destroy, so a long-running caller waits on
+ * every ticket it is given, polled or not. */
 int kf_server_wait(kf_server *s, uint64_t ticket, double timeout_s);
 
 /* paused != 0: admit and launch nothing new (work already on the device
