@@ -39,7 +39,11 @@
  *
  * Ownership and execution.  Every data pointer is a DEVICE pointer owned by
  * the caller (allocated e.g. by PyTorch); the library allocates nothing per
- * call and keeps no reference after the call returns.  Calls are enqueued on
+ * call and keeps no reference after the call returns.  Managed memory and
+ * page-locked host memory are accepted too (each array is checked against
+ * its allocation); calls with such an array run the one-thread-per-track
+ * kernels, whose plain loads and stores reach them, never the bulk copies
+ * of the staged kernels.  Workspaces and arenas must be device memory.  Calls are enqueued on
  * `stream` (a cudaStream_t; NULL = the legacy default stream) and return
  * without synchronising.  Input and output may alias exactly (in place:
  * state_in == state_out and/or cov_in == cov_out); any other overlap is
@@ -109,7 +113,9 @@ typedef struct {
                                ill-conditioned tracks there and a second,
                                short kernel redoes just those (KF_ERR_ARG
                                when status is NULL).  The host-array entry
-                               points and the server use their own.         */
+                               points and the server use their own (the
+                               host-array direct path: the workspace, or
+                               the no-allocation call's staging buffer).    */
 
 typedef struct {
     float    bz;        /* field along +z in tesla                          */
@@ -161,29 +167,45 @@ int kf_p2r_propagate_update(const kf_params *params, kf_layout layout,
 
 /*
  * kf_p2z_propagate_update_host / kf_p2r_propagate_update_host -- the same
- * steps on HOST arrays, the host<->device copies included (the paper's p2z
- * throughput counts the transfers: section 4, Figure 6).
+ * steps on HOST arrays, the host<->device transfers included (the paper's
+ * p2z throughput counts the transfers: section 4, Figure 6).
  *   state_in ... status   HOST pointers with the layouts and sizes of the
  *                         device call (AoSoA arrays padded to whole blocks;
  *                         the padding of the output arrays may be
- *                         overwritten).  Page-locked (pinned) memory lets
- *                         the copies run asynchronously; pageable memory
- *                         works but the driver stages it.  surf is a host
- *                         scalar (surf_per_track == 0) or host [n] array.
+ *                         overwritten).  surf is a host scalar
+ *                         (surf_per_track == 0) or host [n] array.
  *   workspace             DEVICE buffer owned by the caller, 256-byte
  *                         aligned, of at least
- *                         kf_host_workspace_bytes(layout, chunk_tracks) bytes
- *   chunk_tracks          tracks per pipeline chunk (rounded up to the AoSoA
- *                         width); 0 selects 262144
+ *                         kf_host_workspace_bytes(layout, chunk_tracks)
+ *                         bytes; used by the copy path only (and by the
+ *                         direct path for KF_ADAPTIVE's redo marks when
+ *                         status is NULL: n bytes), else may be NULL
+ *   chunk_tracks          copy path: tracks per pipeline chunk (rounded up
+ *                         to the AoSoA width); 0 selects 262144
  *   stream                the work starts after what is already queued on
  *                         `stream`, and work queued on `stream` afterwards
  *                         starts after it: synchronise `stream` before
  *                         reading the host outputs.
- * The batch is processed in chunks alternating between two streams the
- * library creates once per device (kept until exit); while one chunk runs
- * its kernel and copies out, the next copies in.  Calls on one device are
- * serialised by a lock while they enqueue.  Errors as for the device calls;
- * host pointers are not range-checked (their sizes are the caller's duty).
+ * Two paths (kf_set_host_path chooses; by default the direct one wherever
+ * it applies):
+ *   direct  every array is reachable in place from the GPU -- page-locked
+ *           (pinned) memory, or any mapped host memory on a device that
+ *           walks the host page tables (cudaDevAttrPageableMemoryAccess-
+ *           UsesHostPageTables: Grace-Blackwell, Grace-Hopper) -- and every
+ *           float array 4-byte aligned: the kernel reads the inputs from and
+ *           writes the results to the caller's arrays over the CPU-GPU link,
+ *           on `stream`; no copies, no workspace.  Output arrays must be
+ *           writable memory (a read-only mapping faults the kernel).
+ *   copy    otherwise: the batch is processed in chunks alternating between
+ *           two streams the library creates once per device (kept until
+ *           exit); while one chunk runs its kernel and copies out, the next
+ *           copies in.  Page-locked memory lets the copies run
+ *           asynchronously; pageable memory works but the driver stages it.
+ *           Calls on one device are serialised by a lock while they enqueue.
+ * Errors as for the device calls.  Page-locked and device arrays are range-
+ * checked against their allocations; pageable arrays only against the
+ * process's mappings (KF_ERR_ARG when a range holds unmapped pages): their
+ * sizes are otherwise the caller's duty.
  */
 int kf_p2z_propagate_update_host(const kf_params *params, kf_layout layout,
                                  const float *state_in, const float *cov_in,
@@ -203,9 +225,26 @@ int kf_p2r_propagate_update_host(const kf_params *params, kf_layout layout,
                                  void *workspace, int64_t workspace_bytes,
                                  int64_t chunk_tracks, void *stream);
 
-/* Device workspace bytes the host-array calls need for `layout` and
- * `chunk_tracks` (0 = default chunk); -1 for an invalid layout. */
+/* Device workspace bytes the host-array calls' copy path needs for `layout`
+ * and `chunk_tracks` (0 = default chunk); -1 for an invalid layout. */
 int64_t kf_host_workspace_bytes(kf_layout layout, int64_t chunk_tracks);
+
+/*
+ * kf_set_host_path -- how the host-array calls (the _host pair and
+ * kf_propagate_update_host_noalloc) move data, for all later calls in this
+ * process:
+ *   KF_HOST_AUTO    (default) direct where every array allows it, else copy;
+ *   KF_HOST_COPY    always the chunked copy path;
+ *   KF_HOST_DIRECT  always direct: KF_ERR_ARG when an array is not reachable
+ *                   in place (or, for KF_ADAPTIVE without a status array,
+ *                   when there is no device scratch for the redo marks).
+ * The results are the same on either path, bit for bit.  Returns KF_ERR_ARG
+ * for an unknown mode.
+ */
+#define KF_HOST_AUTO   0
+#define KF_HOST_COPY   1
+#define KF_HOST_DIRECT 2
+int kf_set_host_path(int32_t mode);
 
 /* Step kinds for entry points that take the kind as an argument. */
 #define KF_P2Z 0
@@ -307,6 +346,11 @@ int kf_kalman_chain(const kf_params *params, kf_layout layout, float *state,
  *                   chunk by chunk.
  *   stream          all copies and kernels run on this stream, in order;
  *                   synchronise it before reading the host outputs.
+ * The direct path of the _host calls applies here too (kf_set_host_path):
+ * where every array is reachable in place the kernel works on the caller's
+ * arrays and the staging buffer is not used, except as the redo marks of
+ * KF_ADAPTIVE without a status array (n <= KF_NOALLOC_STAGING_BYTES; larger
+ * such calls take the copy path).
  *
  * Set-up: the first call on a device looks up the device address of the
  * staging buffer with that device current (cudaGetSymbolAddress).  Make that
@@ -509,9 +553,9 @@ int kf_set_staged_ctas_per_sm(int32_t ctas);
 #define KF_DEVERR_TIMEOUT 1u
 int kf_take_device_error(unsigned int *error_bits);
 
-/* Library version as MAJOR*10000 + MINOR*100 + PATCH (0.2.0 = 200; the
+/* Library version as MAJOR*10000 + MINOR*100 + PATCH (0.3.0 = 300; the
  * minor number grows with every change of a declared struct or function). */
-#define KF_VERSION 200
+#define KF_VERSION 300
 int kf_version(void);
 
 /* Message of the last KF_ERR_* returned on the calling thread ("" if none). */

@@ -39,12 +39,29 @@ inline int64_t layout_floats(const LayoutDesc &d, int C) {
 }
 
 // KF_OK when [p, p + bytes) is memory a kernel may read or write: device
-// or managed memory lying wholly inside one live allocation, or registered
-// (pinned) host memory.  KF_ERR_ARG for NULL, pageable host memory, an
-// address CUDA does not know, or a range running past the end of its
-// allocation -- so that a wrong pointer or a short buffer is refused on the
-// host instead of faulting the GPU.
-int check_device_range(const void *p, int64_t bytes, const char *name);
+// or managed memory, or page-locked host memory whose device address is its
+// host address, lying wholly inside one live allocation.  KF_ERR_ARG for
+// NULL, pageable host memory, an address CUDA does not know, or a range
+// running past the end of its allocation -- so that a wrong pointer or a
+// short buffer is refused on the host instead of faulting the GPU.  When
+// `not_device` is given it is set for page-locked host and managed memory:
+// those arrays are read with plain loads by the one-thread-per-track
+// kernels, never by the bulk copies of the staged kernels.
+int check_device_range(const void *p, int64_t bytes, const char *name,
+                       bool *not_device = nullptr);
+
+// As check_device_range, but only device memory proper (cudaMalloc'd or
+// from a device memory pool) is accepted: workspaces and arenas.
+int check_device_memory(const void *p, int64_t bytes, const char *name);
+
+// For the host-array entries: KF_OK with *direct set when a kernel on the
+// current device can read and write [p, p + bytes) in place -- device,
+// managed or page-locked memory as check_device_range accepts it, or, on a
+// device that reaches pageable memory through the host page tables, host
+// memory that is mapped over the whole range -- and `align` divides p;
+// KF_OK with *direct cleared when only the copy path can serve it; KF_ERR_ARG
+// for NULL or a range that is short or not mapped.
+int host_reach(const void *p, int64_t bytes, int align, const char *name, bool *direct);
 
 // True when [a, a+na) and [b, b+nb) overlap but do not coincide.
 inline bool partial_overlap(const void *a, int64_t na, const void *b, int64_t nb) {

@@ -1,14 +1,25 @@
 // kf_host.cu -- the single step on HOST arrays, with the host<->device
-// copies inside the call (the paper's p2z measurement includes the data
+// transfers inside the call (the paper's p2z measurement includes the data
 // transfers; section 4, Figure 6 shows them on one stream before and after
 // the kernel).
 //
-// GB300 design: instead of one stream doing copy-in, kernel, copy-out in
-// sequence, the batch is cut into chunks that alternate between two
+// GB300 design, two paths.
+//
+// Direct: on a Grace-Blackwell node the GPU reaches host memory over the
+// coherent CPU-GPU link, page-locked memory always and pageable memory too
+// where the device walks the host page tables.  Then the step kernel itself
+// reads the inputs from and writes the results to the caller's arrays: no
+// copy engine, no staging buffer, and both link directions busy for the
+// whole kernel (copy engines measured 211 GB/s in, 193 GB/s out and 315 GB/s
+// both ways at once on GB300; one kernel reading 139 MB and writing 105 MB
+// of page-locked memory moved 316-327 GB/s, pageable 271-278 GB/s).
+//
+// Copy: otherwise the batch is cut into chunks that alternate between two
 // library-owned streams.  While chunk c runs its kernel and copies its
 // results out, chunk c+1 is already copying in on the other stream, so
 // both copy directions and the kernels overlap.  The device buffers for the
 // two chunks in flight live in a caller-provided workspace.
+#include <atomic>
 #include <cstring>
 #include <mutex>
 
@@ -16,6 +27,7 @@
 
 #include "kf_common.cuh"
 #include "kf_device.cuh"
+#include "kf_host.cuh"
 #include "kf_step.cuh"
 
 namespace kf {
@@ -115,6 +127,61 @@ cudaError_t copy_chunk(void *dst, const void *src, int C, const LayoutDesc &d, i
   return cudaMemcpyAsync(static_cast<float *>(dst) + first, src, bytes, cudaMemcpyDefault, s);
 }
 
+std::atomic<int> g_host_path{KF_HOST_AUTO};
+
+}  // namespace
+
+int host_path_mode() { return g_host_path.load(std::memory_order_relaxed); }
+
+int host_direct(int kind, const kf_params &params, const LayoutDesc &d, const HostArrays &h,
+                uint8_t *scratch, int64_t scratch_bytes, cudaStream_t s, bool *taken) {
+  *taken = false;
+  const int mode = host_path_mode();
+  if (mode == KF_HOST_COPY) return KF_OK;
+  const int64_t b6 = 4 * layout_floats(d, 6), b21 = 4 * layout_floats(d, 21);
+  const void *ptrs[] = {h.state_in, h.cov_in, h.state_out, h.cov_out, h.charge,
+                        h.hit,      h.hit_cov, h.surf,     h.status};
+  const int64_t bytes[] = {b6, b21, b6, b21, d.n, 4 * layout_floats(d, 3), b6,
+                           h.surf_per_track ? 4 * d.n : 4, d.n};
+  const int align[] = {4, 4, 4, 4, 1, 4, 4, 4, 1};
+  const char *names[] = {"state_in", "cov_in", "state_out", "cov_out", "charge",
+                         "hit",      "hit_cov", "surf",     "status"};
+  const int count = h.status ? 9 : 8;
+  for (int k = 0; k < count; ++k) {
+    bool direct = false;
+    if (int rc = host_reach(ptrs[k], bytes[k], align[k], names[k], &direct)) return rc;
+    if (!direct) {
+      if (mode == KF_HOST_AUTO) return KF_OK;
+      return set_error(KF_ERR_ARG,
+                       "KF_HOST_DIRECT: %s is not reachable in place from this device "
+                       "(pageable memory on a device without host page-table access, or "
+                       "misaligned)",
+                       names[k]);
+    }
+  }
+  if (partial_overlap(h.state_in, b6, h.state_out, b6) ||
+      partial_overlap(h.cov_in, b21, h.cov_out, b21))
+    return set_error(KF_ERR_ARG, "input and output overlap without coinciding");
+  uint8_t *status = h.status;
+  if (!status && params.precision == KF_ADAPTIVE) {
+    if (!scratch || scratch_bytes < d.n) {
+      if (mode == KF_HOST_AUTO) return KF_OK;
+      return set_error(KF_ERR_ARG,
+                       "KF_HOST_DIRECT with KF_ADAPTIVE and no status array needs %lld bytes "
+                       "of device scratch for the redo marks",
+                       (long long)d.n);
+    }
+    status = scratch;
+  }
+  StepArgs a{h.state_in, h.cov_in, h.state_out, h.cov_out, h.charge, h.hit, h.hit_cov, h.surf,
+             status,     d.n,      d.soa,       d.lw,      params.bz, h.surf_per_track};
+  if (int rc = launch_step_kernel(kind, params.precision, a, s, /*plain_loads=*/true)) return rc;
+  *taken = true;
+  return KF_OK;
+}
+
+namespace {
+
 int run_host(int kind, const kf_params *params, kf_layout layout, const float *state_in,
              const float *cov_in, float *state_out, float *cov_out, const int8_t *charge,
              const float *hit, const float *hit_cov, const float *surf, int32_t surf_per_track,
@@ -133,6 +200,22 @@ int run_host(int kind, const kf_params *params, kf_layout layout, const float *s
   if (surf_per_track != 0 && surf_per_track != 1)
     return set_error(KF_ERR_ARG, "surf_per_track must be 0 or 1");
   if (chunk_tracks < 0) return set_error(KF_ERR_ARG, "chunk_tracks < 0");
+  cudaStream_t caller = static_cast<cudaStream_t>(stream);
+  {
+    const HostArrays h{state_in, cov_in, state_out, cov_out, charge,
+                       hit,      hit_cov, surf,     surf_per_track, status};
+    // KF_ADAPTIVE without a status array: the workspace holds the redo marks
+    uint8_t *scratch = nullptr;
+    if (!status && params->precision == KF_ADAPTIVE && workspace && workspace_bytes >= d.n) {
+      if (check_device_memory(workspace, d.n, "workspace") == KF_OK)
+        scratch = static_cast<uint8_t *>(workspace);
+      clear_error();
+    }
+    bool taken = false;
+    if (int rc = host_direct(kind, *params, d, h, scratch, workspace_bytes, caller, &taken))
+      return rc;
+    if (taken) return KF_OK;
+  }
   const int64_t chunk = effective_chunk(d, chunk_tracks);
   const Slot sl = slot_layout(chunk);
   if (workspace_bytes < 2 * sl.bytes)
@@ -140,12 +223,11 @@ int run_host(int kind, const kf_params *params, kf_layout layout, const float *s
                      (long long)workspace_bytes, (long long)(2 * sl.bytes));
   if (reinterpret_cast<uintptr_t>(workspace) & 255u)
     return set_error(KF_ERR_ARG, "workspace must be 256-byte aligned");
-  if (int rc = check_device_range(workspace, 2 * sl.bytes, "workspace")) return rc;
+  if (int rc = check_device_memory(workspace, 2 * sl.bytes, "workspace")) return rc;
 
   std::lock_guard<std::mutex> lock(g_pipe_mu);
   HostPipe *pipe = nullptr;
   if (int rc = get_pipe(&pipe)) return rc;
-  cudaStream_t caller = static_cast<cudaStream_t>(stream);
   if (int rc = check_cuda(cudaEventRecord(pipe->fork, caller), "cudaEventRecord")) return rc;
   for (int i = 0; i < 2; ++i)
     if (int rc = check_cuda(cudaStreamWaitEvent(pipe->s[i], pipe->fork, 0), "cudaStreamWaitEvent"))
@@ -229,4 +311,12 @@ extern "C" int kf_p2r_propagate_update_host(const kf_params *params, kf_layout l
   return kf::run_host(kf::kP2r, params, layout, state_in, cov_in, state_out, cov_out, charge, hit,
                       hit_cov, r_surf, surf_per_track, status, workspace, workspace_bytes,
                       chunk_tracks, stream);
+}
+
+extern "C" int kf_set_host_path(int32_t mode) {
+  kf::clear_error();
+  if (mode != KF_HOST_AUTO && mode != KF_HOST_COPY && mode != KF_HOST_DIRECT)
+    return kf::set_error(KF_ERR_ARG, "unknown host path mode %d", mode);
+  kf::g_host_path.store(mode, std::memory_order_relaxed);
+  return KF_OK;
 }

@@ -9,6 +9,11 @@
 // workspace; this variant instead stages the chunks through a fixed buffer
 // that the library declares in device memory, so the call allocates nothing.
 //
+// Where every array is reachable in place from the GPU (page-locked memory,
+// or pageable memory on a device that walks the host page tables) the
+// shared direct path of the host-array calls serves the call instead, and
+// nothing is staged.
+//
 // The staging buffer is a file-scope __device__ array: every GPU that loads
 // the library holds it until the process exits.  Host code cannot use the
 // array's name as a device address (it is a host-side stand-in), so its
@@ -20,6 +25,7 @@
 
 #include "kf_common.cuh"
 #include "kf_device.cuh"
+#include "kf_host.cuh"
 #include "kf_step.cuh"
 
 namespace kf {
@@ -133,6 +139,24 @@ extern "C" int kf_propagate_update_host_noalloc(int32_t kind, const kf_params *p
   if (surf_per_track != 0 && surf_per_track != 1)
     return set_error(KF_ERR_ARG, "surf_per_track must be 0 or 1");
 
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  {
+    // arrays reachable in place: the kernel works on them, nothing is staged
+    // (the staging buffer holds KF_ADAPTIVE's redo marks when status is NULL)
+    const HostArrays h{state_in, cov_in, state_out, cov_out, charge,
+                       hit,      hit_cov, surf,     surf_per_track, status};
+    uint8_t *scratch = nullptr;
+    if (!status && params->precision == KF_ADAPTIVE && d.n <= KF_NOALLOC_STAGING_BYTES) {
+      unsigned char *staging = nullptr;
+      if (int rc = staging_address(&staging)) return rc;
+      scratch = staging;
+    }
+    bool taken = false;
+    if (int rc = host_direct(kind, *params, d, h, scratch, KF_NOALLOC_STAGING_BYTES, s, &taken))
+      return rc;
+    if (taken) return KF_OK;
+  }
+
   // Chunk: the requested size (default: the capacity), a whole number of
   // AoSoA blocks, never more than the staged layout holds.
   const int64_t W = d.soa ? 1 : (int64_t(1) << d.lw);
@@ -155,7 +179,6 @@ extern "C" int kf_propagate_update_host_noalloc(int32_t kind, const kf_params *p
   // Everything runs on the caller's stream, chunk after chunk through the one
   // staging area: stream order keeps a chunk's copies-in behind the previous
   // chunk's copies-out.
-  cudaStream_t s = static_cast<cudaStream_t>(stream);
   for (int64_t c0 = 0; c0 < d.n; c0 += chunk) {
     const int64_t m = (d.n - c0 < chunk) ? d.n - c0 : chunk;
     LayoutDesc dc = d;

@@ -524,7 +524,7 @@ extern "C" int kf_server_create(const kf_server_config *cfg, kf_server **out) {
   if (reinterpret_cast<uintptr_t>(cfg->arena) & 255u)
     return set_error(KF_ERR_ARG, "arena must be 256-byte aligned");
   if (int rc = check_cuda(cudaSetDevice(cfg->device), "cudaSetDevice")) return rc;
-  if (int rc = check_device_range(cfg->arena, cfg->arena_bytes, "arena")) return rc;
+  if (int rc = check_device_memory(cfg->arena, cfg->arena_bytes, "arena")) return rc;
 
   kf_server *s = new kf_server;
   s->cfg = *cfg;

@@ -138,6 +138,7 @@ static int launch_step(const kf_params *params, kf_layout layout, const float *s
     return set_error(KF_ERR_ARG, "float arrays must be 16-byte aligned");
   if (surf_per_track != 0 && surf_per_track != 1)
     return set_error(KF_ERR_ARG, "surf_per_track must be 0 or 1");
+  bool plain_loads = false;  // some array in host or managed memory
   {
     const int64_t b6 = 4 * layout_floats(d, 6), b21 = 4 * layout_floats(d, 21);
     const void *ptrs[] = {state_in, cov_in, state_out, cov_out, charge, hit, hit_cov, surf};
@@ -145,10 +146,16 @@ static int launch_step(const kf_params *params, kf_layout layout, const float *s
                              surf_per_track ? 4 * d.n : 4};
     const char *names[] = {"state_in", "cov_in", "state_out", "cov_out",
                            "charge",   "hit",    "hit_cov",   "surf"};
-    for (int k = 0; k < 8; ++k)
-      if (int rc = check_device_range(ptrs[k], bytes[k], names[k])) return rc;
-    if (status)
-      if (int rc = check_device_range(status, d.n, "status")) return rc;
+    for (int k = 0; k < 8; ++k) {
+      bool nd = false;
+      if (int rc = check_device_range(ptrs[k], bytes[k], names[k], &nd)) return rc;
+      plain_loads |= nd;
+    }
+    if (status) {
+      bool nd = false;
+      if (int rc = check_device_range(status, d.n, "status", &nd)) return rc;
+      plain_loads |= nd;
+    }
     if (!status && params->precision == KF_ADAPTIVE)
       return set_error(KF_ERR_ARG, "KF_ADAPTIVE needs a status array (its redo pass reads it)");
   }
@@ -158,7 +165,8 @@ static int launch_step(const kf_params *params, kf_layout layout, const float *s
 
   StepArgs a{state_in, cov_in, state_out, cov_out, charge, hit, hit_cov, surf, status,
              d.n,      d.soa,  d.lw,      params->bz, surf_per_track};
-  return launch_step_kernel(KIND, params->precision, a, static_cast<cudaStream_t>(stream));
+  return launch_step_kernel(KIND, params->precision, a, static_cast<cudaStream_t>(stream),
+                            plain_loads);
 }
 
 namespace {
@@ -168,22 +176,27 @@ std::atomic<int> g_staged_ctas{0};
 
 int step_kernel_mode() { return g_step_mode.load(std::memory_order_relaxed); }
 
-static int launch_step_main(int kind, int precision, const StepArgs &a, cudaStream_t s);
+static int launch_step_main(int kind, int precision, const StepArgs &a, cudaStream_t s,
+                            bool plain_loads);
 
-int launch_step_kernel(int kind, int precision, const StepArgs &a, cudaStream_t s) {
+int launch_step_kernel(int kind, int precision, const StepArgs &a, cudaStream_t s,
+                       bool plain_loads) {
   if (a.n == 0) return KF_OK;
   if (precision == KF_ADAPTIVE && !a.status)
     return set_error(KF_ERR_ARG, "KF_ADAPTIVE needs a status array (its redo pass reads it)");
-  if (int rc = launch_step_main(kind, precision, a, s)) return rc;
+  if (int rc = launch_step_main(kind, precision, a, s, plain_loads)) return rc;
   return precision == KF_ADAPTIVE ? launch_redo_pass(kind, a, s) : KF_OK;
 }
 
-static int launch_step_main(int kind, int precision, const StepArgs &a, cudaStream_t s) {
-  // The staged kernel copies whole tiles with 16-byte-aligned bulk copies:
-  // any AoSoA layout, SoA when n is a multiple of 4.
-  const bool staged_ok = !a.soa || (a.n & 3) == 0;
+static int launch_step_main(int kind, int precision, const StepArgs &a, cudaStream_t s,
+                            bool plain_loads) {
+  // The staged kernel copies whole tiles of device memory with 16-byte-
+  // aligned bulk copies: any AoSoA layout, SoA when n is a multiple of 4.
+  const bool staged_ok = !plain_loads && (!a.soa || (a.n & 3) == 0);
   LaunchConfig cfg{staged_ok ? KF_STEP_STAGED : KF_STEP_DIRECT, 256, 2};
-  if (const LaunchConfig *o = thread_override()) {
+  if (plain_loads) {
+    // host or managed memory: the defaults above (direct, 256 threads)
+  } else if (const LaunchConfig *o = thread_override()) {
     cfg = *o;
   } else {
     const int mode = step_kernel_mode();

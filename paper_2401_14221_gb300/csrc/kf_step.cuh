@@ -136,8 +136,11 @@ struct LaunchConfig {
 // Launch the p2z (kind 0) or p2r (kind 1) step kernel for `a` on stream s
 // with the given KF_* precision variant.  The shape comes from, in order:
 // the autotuner's per-thread override while it measures, the process-wide
-// kf_set_step_kernel mode, the tuning cache, the defaults.
-int launch_step_kernel(int kind, int precision, const StepArgs &a, cudaStream_t s);
+// kf_set_step_kernel mode, the tuning cache, the defaults.  plain_loads
+// (arrays in host or managed memory) overrides all of them: the
+// one-thread-per-track kernel, 256 threads per CTA.
+int launch_step_kernel(int kind, int precision, const StepArgs &a, cudaStream_t s,
+                       bool plain_loads = false);
 
 // Second pass of KF_ADAPTIVE: redo in FP64 every track whose status the
 // step kernel marked with kRedo (those tracks' outputs are not yet written).

@@ -188,10 +188,17 @@ extern "C" int kf_propagate_update_compressed(
                            surf_per_track ? 4 * d.n : 4};
   const char *names[] = {"state_in", "sigma_in", "rho_in", "state_out", "sigma_out",
                          "rho_out",  "charge",   "hit",    "hit_cov",   "surf"};
-  for (int k = 0; k < 10; ++k)
-    if (int rc = check_device_range(ptrs[k], bytes[k], names[k])) return rc;
-  if (status)
-    if (int rc = check_device_range(status, d.n, "status")) return rc;
+  bool plain_loads = false;  // some array in host or managed memory
+  for (int k = 0; k < 10; ++k) {
+    bool nd = false;
+    if (int rc = check_device_range(ptrs[k], bytes[k], names[k], &nd)) return rc;
+    plain_loads |= nd;
+  }
+  if (status) {
+    bool nd = false;
+    if (int rc = check_device_range(status, d.n, "status", &nd)) return rc;
+    plain_loads |= nd;
+  }
   if (!status && params->precision == KF_ADAPTIVE)
     return set_error(KF_ERR_ARG, "KF_ADAPTIVE needs a status array (its redo pass reads it)");
   if (partial_overlap(state_in, b6, state_out, b6) || partial_overlap(sigma_in, b6, sigma_out, b6) ||
@@ -207,8 +214,9 @@ extern "C" int kf_propagate_update_compressed(
   if (blocks > 0x7fffffffLL) return set_error(KF_ERR_ARG, "n too large for one launch");
   const unsigned g = (unsigned)blocks;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  // AoSoA with a float-arithmetic variant: the staged kernel (same results)
-  const bool staged = !d.soa && step_kernel_mode() != KF_STEP_DIRECT &&
+  // AoSoA in device memory with a float-arithmetic variant: the staged
+  // kernel (same results)
+  const bool staged = !d.soa && !plain_loads && step_kernel_mode() != KF_STEP_DIRECT &&
                       (params->precision == KF_FP32 || params->precision == KF_JOSEPH ||
                        params->precision == KF_ADAPTIVE);
   if (staged) {

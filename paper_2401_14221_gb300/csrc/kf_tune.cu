@@ -181,8 +181,8 @@ extern "C" int kf_autotune_chain(const kf_params *params, kf_layout layout, floa
   if (int rc = check_layout(layout, &d)) return rc;
   if (d.n == 0 || L <= 0) return set_error(KF_ERR_ARG, "nothing to tune");
   const int64_t b6 = 4 * layout_floats(d, 6), b21 = 4 * layout_floats(d, 21);
-  if (int rc = check_device_range(state_scratch, b6, "state_scratch")) return rc;
-  if (int rc = check_device_range(cov_scratch, b21, "cov_scratch")) return rc;
+  if (int rc = check_device_memory(state_scratch, b6, "state_scratch")) return rc;
+  if (int rc = check_device_memory(cov_scratch, b21, "cov_scratch")) return rc;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   // keep the start state; restore it before every call and at the end
   if (int rc = check_cuda(cudaMemcpyAsync(state_scratch, state, b6, cudaMemcpyDeviceToDevice, s),

@@ -139,6 +139,8 @@ def load():
     lib.kf_set_step_kernel.restype = ctypes.c_int
     lib.kf_set_staged_ctas_per_sm.argtypes = [ctypes.c_int32]
     lib.kf_set_staged_ctas_per_sm.restype = ctypes.c_int
+    lib.kf_set_host_path.argtypes = [ctypes.c_int32]
+    lib.kf_set_host_path.restype = ctypes.c_int
     lib.kf_take_device_error.argtypes = [ctypes.POINTER(ctypes.c_uint)]
     lib.kf_take_device_error.restype = ctypes.c_int
     lib.kf_version.restype = ctypes.c_int
@@ -236,8 +238,10 @@ def _step_host(fn_name, params, layout, state_in, cov_in, state_out, cov_out, ch
     lib = load()
     f32, i8, u8 = torch.float32, torch.int8, torch.uint8
     ws = _ptr(workspace, "workspace")
-    ws_bytes = workspace.numel() * workspace.element_size() if isinstance(workspace, torch.Tensor) \
-        else int(1 << 62)
+    if isinstance(workspace, torch.Tensor):
+        ws_bytes = workspace.numel() * workspace.element_size()
+    else:  # a raw pointer: its extent is checked by the library; None: no workspace
+        ws_bytes = int(1 << 62) if isinstance(workspace, int) else 0
     rc = getattr(lib, fn_name)(
         ctypes.byref(params), layout,
         _host_ptr(state_in, "state_in", f32), _host_ptr(cov_in, "cov_in", f32),
@@ -347,6 +351,14 @@ def kf_set_step_kernel(mode: int) -> None:
 def kf_set_staged_ctas_per_sm(ctas: int) -> None:
     """C-ABI kf_set_staged_ctas_per_sm: 1..3 CTAs per SM under KF_STEP_STAGED, 0 = default."""
     _check(load().kf_set_staged_ctas_per_sm(int(ctas)))
+
+
+KF_HOST_AUTO, KF_HOST_COPY, KF_HOST_DIRECT = 0, 1, 2
+
+
+def kf_set_host_path(mode: int) -> None:
+    """C-ABI kf_set_host_path: KF_HOST_AUTO / KF_HOST_COPY / KF_HOST_DIRECT."""
+    _check(load().kf_set_host_path(int(mode)))
 
 
 def kf_take_device_error() -> int:

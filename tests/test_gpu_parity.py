@@ -49,6 +49,26 @@ def step_kernel(request, dev):
     kf.kf_set_step_kernel(kf.KF_STEP_AUTO)
 
 
+@pytest.fixture(params=[kf.KF_HOST_COPY, kf.KF_HOST_DIRECT], ids=["copy", "direct"])
+def host_path(request, dev):
+    """The host-array calls' data path: chunked copies through the workspace,
+    or the kernel on the host arrays in place."""
+    kf.kf_set_host_path(request.param)
+    yield request.param
+    kf.kf_set_host_path(kf.KF_HOST_AUTO)
+
+
+def run_host_or_skip(hb, host_path, pinned, **kw):
+    """hb.run(), skipping direct runs on pageable memory where the device
+    cannot reach it (no host page-table access)."""
+    try:
+        hb.run(**kw)
+    except kf.KfError as e:
+        if host_path == kf.KF_HOST_DIRECT and not pinned and "not reachable" in str(e):
+            pytest.skip("this device does not reach pageable host memory")
+        raise
+
+
 @pytest.fixture(scope="module")
 def w_p2z():
     return W.single_step_p2z()
@@ -358,12 +378,15 @@ def test_short_buffer_is_refused(dev):
 
 @pytest.mark.parametrize("layout", [(kf.KF_SOA, 0), (kf.KF_AOSOA, 64)])
 @pytest.mark.parametrize("pinned", [True, False])
-def test_host_array_entry_matches_device_entry(dev, layout, pinned):
-    # 99,999 tracks in chunks of 16,384: seven chunks over both pipeline
-    # slots, the last one ragged.  Same kernel, so results are bitwise equal.
+def test_host_array_entry_matches_device_entry(dev, layout, pinned, host_path):
+    # Copy path: 99,999 tracks in chunks of 16,384, seven chunks over both
+    # pipeline slots, the last one ragged.  Direct path: the kernel reads and
+    # writes the host arrays in place (page-locked, or pageable through the
+    # host page tables).  The arithmetic is the same, so results are bitwise
+    # equal to the device entry's.
     for w in (W.make_p2r(3, 33333, seed=15), W.make_p2z(99999, seed=16)):
         hb = kf.host_upload(w, layout[0], layout[1], dev, chunk_tracks=16384, pinned=pinned)
-        hb.run()
+        run_host_or_skip(hb, host_path, pinned)
         torch.cuda.synchronize()
         got = hb.download()
         ref = run(w, dev, layout).download()
@@ -379,9 +402,9 @@ def test_host_array_entry_matches_device_entry(dev, layout, pinned):
 
 @pytest.mark.parametrize("n", [1, 33, 4097, 300001])
 @pytest.mark.parametrize("layout", [(kf.KF_SOA, 0), (kf.KF_AOSOA, 128)])
-def test_host_entry_default_chunk(dev, n, layout):
+def test_host_entry_default_chunk(dev, n, layout, host_path):
     # the default chunk (262,144 tracks): one chunk, or two with the last
-    # one ragged
+    # one ragged; and the same sizes in place
     w = W.make_p2r(1, n, seed=18)
     hb = kf.host_upload(w, layout[0], layout[1], dev, pinned=True)
     hb.run()
@@ -393,10 +416,11 @@ def test_host_entry_default_chunk(dev, n, layout):
 
 
 @pytest.mark.parametrize("entry", ["workspace", "noalloc"])
-def test_host_entries_run_adaptive_without_a_status_array(dev, entry):
+def test_host_entries_run_adaptive_without_a_status_array(dev, entry, host_path):
     # KF_ADAPTIVE needs a status array on the device for its redo pass; the
-    # host-array entry points use their own staging for it, so the caller may
-    # pass none.  Results equal the device entry's bit for bit.
+    # host-array entry points use their own staging for it (on the direct
+    # path: the workspace, or the no-allocation call's staging buffer), so
+    # the caller may pass none.  Results equal the device entry's bit for bit.
     w = grazing_p2r()
     lay = (kf.KF_AOSOA, 32)
     ref = run(w, dev, lay, kf.KF_ADAPTIVE).download()
@@ -420,9 +444,101 @@ def test_host_entry_rejects_small_workspace(dev):
     w = W.make_p2z(5000, seed=17)
     hb = kf.host_upload(w, kf.KF_SOA, 0, dev, chunk_tracks=1024)
     hb.workspace = hb.workspace[: hb.workspace.numel() // 2]
-    with pytest.raises(kf.KfError) as e:
-        hb.run()
-    assert e.value.code == kf.KF_ERR_ARG
+    kf.kf_set_host_path(kf.KF_HOST_COPY)
+    try:
+        with pytest.raises(kf.KfError) as e:
+            hb.run()
+        assert e.value.code == kf.KF_ERR_ARG
+    finally:
+        kf.kf_set_host_path(kf.KF_HOST_AUTO)
+
+
+@pytest.mark.parametrize("precision", [kf.KF_FP32, kf.KF_JOSEPH, kf.KF_FP64, kf.KF_ADAPTIVE])
+def test_host_direct_path_needs_no_workspace(dev, precision):
+    # In place on page-locked memory the call needs no device memory at all
+    # (KF_ADAPTIVE with its status array given).  Results equal the device
+    # entry's bit for bit, for every precision variant.
+    w = grazing_p2r() if precision == kf.KF_ADAPTIVE else W.make_p2r(2, 5001, seed=31)
+    lay = (kf.KF_AOSOA, 32)
+    ref = run(w, dev, lay, precision).download()
+    hb = kf.host_upload(w, lay[0], lay[1], dev, pinned=True)
+    hb.workspace = None
+    kf.kf_set_host_path(kf.KF_HOST_DIRECT)
+    try:
+        hb.run(precision)
+        torch.cuda.synchronize()
+    finally:
+        kf.kf_set_host_path(kf.KF_HOST_AUTO)
+    got = hb.download()
+    for a, c in zip(ref, got):
+        assert np.array_equal(a, c)
+
+
+def test_host_direct_path_refusals(dev):
+    w = W.make_p2r(1, 4096, seed=32)
+    lay = (kf.KF_SOA, 0)
+    hb = kf.host_upload(w, lay[0], lay[1], dev, pinned=True)
+    params = kf.make_params(w.bz, kf.KF_ADAPTIVE)
+    kf.kf_set_host_path(kf.KF_HOST_DIRECT)
+    try:
+        # KF_ADAPTIVE without a status array and without a workspace: no
+        # device memory for the redo marks
+        with pytest.raises(kf.KfError) as e:
+            kf.kf_p2r_propagate_update_host(params, hb.layout, hb.state_in, hb.cov_in,
+                                            hb.state_out, hb.cov_out, hb.charge, hb.hit,
+                                            hb.hit_cov, hb.surf, 1, None, None, 0)
+        assert e.value.code == kf.KF_ERR_ARG
+        # a page-locked array shorter than the layout needs (registered with
+        # its exact extent: 1,024 floats where 21 x 4,096 are needed)
+        short = np.zeros(1024, dtype=np.float32)
+        cudart = torch.cuda.cudart()
+        assert cudart.cudaHostRegister(short.ctypes.data, short.nbytes, 0) == \
+            cudart.cudaError.success
+        try:
+            with pytest.raises(kf.KfError) as e:
+                kf.kf_p2r_propagate_update_host(
+                    kf.make_params(w.bz), hb.layout, hb.state_in, short.ctypes.data,
+                    hb.state_out, hb.cov_out, hb.charge, hb.hit, hb.hit_cov, hb.surf, 1,
+                    hb.status, None, 0)
+            assert e.value.code == kf.KF_ERR_ARG
+            assert "allocation" in kf.kf_last_error_string()
+        finally:
+            cudart.cudaHostUnregister(short.ctypes.data)
+        # a misaligned float array cannot be read in place
+        with pytest.raises(kf.KfError) as e:
+            kf.kf_p2r_propagate_update_host(
+                kf.make_params(w.bz), hb.layout, hb.state_in.data_ptr() + 2, hb.cov_in,
+                hb.state_out, hb.cov_out, hb.charge, hb.hit, hb.hit_cov, hb.surf, 1, hb.status,
+                None, 0)
+        assert e.value.code == kf.KF_ERR_ARG
+    finally:
+        kf.kf_set_host_path(kf.KF_HOST_AUTO)
+    torch.cuda.synchronize()
+
+
+def test_device_entry_on_page_locked_arrays(dev):
+    # Page-locked host arrays given to the device-array entry run the
+    # one-thread-per-track kernel (plain loads), whatever kernel mode is set;
+    # results equal those on device arrays bit for bit.
+    w = W.make_p2r(2, 4100, seed=33)
+    lay = (kf.KF_AOSOA, 32)
+    ref = run(w, dev, lay).download()
+    hb = kf.host_upload(w, lay[0], lay[1], dev, pinned=True)
+    p = kf.make_params(w.bz)
+    kf.kf_set_step_kernel(kf.KF_STEP_STAGED)
+    try:
+        rc = kf.load().kf_p2r_propagate_update(
+            ctypes.byref(p), hb.layout, *[t.data_ptr() for t in (
+                hb.state_in, hb.cov_in, hb.state_out, hb.cov_out, hb.charge, hb.hit, hb.hit_cov,
+                hb.surf)], int(hb.surf.numel() > 1), hb.status.data_ptr(),
+            torch.cuda.current_stream().cuda_stream)
+        assert rc == kf.KF_OK, kf.kf_last_error_string()
+        torch.cuda.synchronize()
+    finally:
+        kf.kf_set_step_kernel(kf.KF_STEP_AUTO)
+    got = hb.download()
+    for a, c in zip(ref, got):
+        assert np.array_equal(a, c)
 
 
 # -------------------------------------------- compressed covariance store

@@ -30,6 +30,15 @@ def dev():
     return torch.device("cuda:0")
 
 
+@pytest.fixture(params=[kf.KF_HOST_COPY, kf.KF_HOST_DIRECT], ids=["copy", "direct"])
+def host_path(request, dev):
+    """Staged through the library's buffer, or the kernel on the host arrays
+    in place (the buffer unused)."""
+    kf.kf_set_host_path(request.param)
+    yield request.param
+    kf.kf_set_host_path(kf.KF_HOST_AUTO)
+
+
 def _noalloc(hb, fill):
     """Run the no-allocation call on the host arrays of `hb`, writing into
     fresh host outputs pre-filled with `fill`; returns SoA results."""
@@ -54,7 +63,7 @@ def _assert_match(got, ref):
 
 
 @pytest.mark.parametrize("layout", [(kf.KF_SOA, 0), (kf.KF_AOSOA, 16), (kf.KF_AOSOA, 128)])
-def test_noalloc_matches_workspace_entry_on_consecutive_calls(dev, layout):
+def test_noalloc_matches_workspace_entry_on_consecutive_calls(dev, layout, host_path):
     # Two consecutive no-allocation calls per workload, and workloads of
     # different kinds and sizes one after another: each call must see only
     # its own data in the shared staging buffer.  75,003 tracks span three
