@@ -64,7 +64,24 @@ __global__ void __launch_bounds__(kThreads, 2)
     mbar_fence_init();
   }
   __syncthreads();
+  // Programmatic dependent launch, with this CTA's first tiles requested
+  // into L2 while the previous kernel drains (a prefetch cannot return data
+  // that kernel has yet to write: the copies after the wait read L2's
+  // current lines).
   asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+  if (warp == kComputeWarps && lane == 0) {
+    const int64_t npre = ntiles < kStages ? ntiles : kStages;
+    for (int64_t k = 0; k < npre; ++k) {
+      int64_t first, m;
+      sch.tile(k, blockIdx.x, a.n, &first, &m);
+      const uint32_t cols = (uint32_t)(((m + W - 1) / W) * W);
+      staged::bulk_prefetch_l2(a.state_in + first * 6, cols * 6 * 4);
+      staged::bulk_prefetch_l2(a.sigma_in + first * 6, cols * 6 * 4);
+      staged::bulk_prefetch_l2(a.rho_in + first * 15, cols * 15 * 2);
+      staged::bulk_prefetch_l2(a.hit + first * 3, cols * 3 * 4);
+      staged::bulk_prefetch_l2(a.hitcov + first * 6, cols * 6 * 4);
+    }
+  }
   asm volatile("griddepcontrol.wait;" ::: "memory");
 
   if (warp == kComputeWarps) {

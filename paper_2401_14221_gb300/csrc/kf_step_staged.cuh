@@ -124,6 +124,11 @@ __device__ __forceinline__ void bulk_g2s(void *sdst, const void *gsrc, uint32_t 
       : "memory");
 }
 
+// Prefetch [gsrc, gsrc + bytes) into L2 (16-byte aligned, multiple of 16).
+__device__ __forceinline__ void bulk_prefetch_l2(const void *gsrc, uint32_t bytes) {
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(gsrc), "r"(bytes) : "memory");
+}
+
 // Tile schedule of the persistent grid (G CTAs).  Full tiles of kT tracks go
 // round-robin (tile k of CTA b is global tile k G + b), so at any moment the
 // grid works on one narrow window of the arrays.  What is left after the
@@ -201,8 +206,31 @@ __global__ void __launch_bounds__(kThreads, CTAS)
   // Programmatic dependent launch: let the next kernel on the stream be
   // scheduled now (its CTAs take SMs as ours retire and set up their
   // barriers), and wait here until the previous kernel has completed and its
-  // writes are visible -- nothing global is touched before this point.
+  // writes are visible -- nothing global is read or written before this
+  // point.  Meanwhile the producer asks L2 for this CTA's first tiles, so
+  // that a CTA that lands on an SM while the previous kernel drains starts
+  // from L2 instead of HBM.  A prefetch only moves lines into L2, the point
+  // where every SM's loads and stores meet, so it cannot return a value the
+  // previous kernel has yet to write: the copies after the wait read
+  // whatever is current.
   asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+  if (warp == kComputeWarps && lane == 0) {
+    const int64_t npre = ntiles < kStages ? ntiles : kStages;
+    for (int64_t k = 0; k < npre; ++k) {
+      int64_t first, m;
+      sch.tile(k, blockIdx.x, a.n, &first, &m);
+      const uint32_t cols = (uint32_t)(((m + GR - 1) / GR) * GR);
+      if constexpr (kSoa) {
+        for (int c = 0; c < 6; ++c) bulk_prefetch_l2(a.state_in + c * a.n + first, cols * 4);
+        for (int e = 0; e < 21; ++e) bulk_prefetch_l2(a.cov_in + e * a.n + first, cols * 4);
+      } else {
+        bulk_prefetch_l2(a.state_in + first * 6, cols * 6 * 4);
+        bulk_prefetch_l2(a.cov_in + first * 21, cols * 21 * 4);
+        bulk_prefetch_l2(a.hit + first * 3, cols * 3 * 4);
+        bulk_prefetch_l2(a.hitcov + first * 6, cols * 6 * 4);
+      }
+    }
+  }
   asm volatile("griddepcontrol.wait;" ::: "memory");
 
   if (warp == kComputeWarps) {
