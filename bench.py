@@ -74,6 +74,9 @@ def parse():
                     help="staged = staged2: 2 CTAs/SM x 3 stages; staged3: 3 CTAs/SM x 2 stages")
     ap.add_argument("--e2e-steps", type=int, default=30)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true",
+                    help="skip the host-array (end-to-end) timing; e2e is then null (for "
+                         "launch lists of the device-resident step alone)")
     ap.add_argument("--no-chain", action="store_true",
                     help="skip the fused-chain vs per-layer-launch comparison")
     ap.add_argument("--chain-steps", type=int, default=10)
@@ -566,8 +569,17 @@ def main():
 
     w = W.make_p2r(NEVTS, NTRKS, seed=shard.rank_seed(1, rank))
 
+    # Launches per CUDA graph.  Inside a graph consecutive launches keep their
+    # programmatic-dependent-launch overlap (the next kernel's CTAs start and
+    # prefetch while the previous one drains); at a graph boundary they do
+    # not, so a longer graph leaves fewer boundaries per launch (measured on
+    # the staged step: 38.7 us per launch with 4 launches per graph, 37.1
+    # with 16, 36.9 with 64).
+    PER_GRAPH = 16
+
     def graph_time(batches, replays):
-        # one launch per batch captured in a CUDA graph, replayed; ms per launch
+        # PER_GRAPH launches cycling over the batches, captured in a CUDA
+        # graph and replayed; ms per launch
         st = torch.cuda.Stream()
         with torch.cuda.stream(st):
             for b in batches:
@@ -575,9 +587,9 @@ def main():
         torch.cuda.synchronize()
         g = torch.cuda.CUDAGraph()
         with torch.cuda.graph(g, stream=st):
-            for b in batches:
-                b.run()
-        for _ in range(5):
+            for k in range(PER_GRAPH):
+                batches[k % len(batches)].run()
+        for _ in range(3):
             g.replay()
         torch.cuda.synchronize()
         a, b_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -586,7 +598,7 @@ def main():
             g.replay()
         b_.record()
         torch.cuda.synchronize()
-        return a.elapsed_time(b_) / (replays * len(batches))
+        return a.elapsed_time(b_) / (replays * PER_GRAPH)
 
     # Kernel x layout sweep (outside the timed region): the direct kernel and
     # the staged kernel (2 or 3 CTAs per SM) on SoA and the AoSoA widths.
@@ -622,7 +634,8 @@ def main():
         kf.kf_set_step_kernel(kf.KF_STEP_AUTO)
         tuned = kf.autotune_step(sets[0])
 
-    # Capture one launch per buffer set in a CUDA graph; replay it.
+    # Capture PER_GRAPH launches cycling over the buffer sets in a CUDA
+    # graph; replay it.
     stream = torch.cuda.Stream()
     graph = None
     try:
@@ -632,21 +645,21 @@ def main():
         torch.cuda.synchronize()
         graph = torch.cuda.CUDAGraph()
         with torch.cuda.graph(graph, stream=stream):
-            for s in sets:
-                s.run()
+            for k in range(PER_GRAPH):
+                sets[k % len(sets)].run()
         torch.cuda.synchronize()
     except Exception as e:  # capture unsupported: eager launches
         print(f"# CUDA graph capture failed ({e}); timing eager launches", file=sys.stderr)
         graph = None
 
-    reps_per_replay = len(sets) if graph is not None else 1
+    reps_per_replay = PER_GRAPH if graph is not None else 1
 
     def run_steps(k):
         if graph is not None:
             for _ in range(k // reps_per_replay):
                 graph.replay()
             for i in range(k % reps_per_replay):
-                sets[i].run()
+                sets[i % len(sets)].run()
         else:
             for i in range(k):
                 sets[i % len(sets)].run()
@@ -709,7 +722,8 @@ def main():
     peak, peak_src = measured_hbm_peak()
     # Batch-size scaling of the same kernel (context: a fixed per-launch cost
     # of ramp, tail and launch gap weighs less on larger batches).  The
-    # 960,000-track arrays are tiled to 4x; two buffer sets rotate.
+    # 960,000-track arrays are cut to a quarter (four buffer sets rotate, 244 MB
+    # in all, more than L2 holds) or tiled to 4x (two sets rotate).
     scaling = []
     if not args.no_scaling:
         import dataclasses
@@ -721,7 +735,7 @@ def main():
             wm = dataclasses.replace(w, n=m, state=tile(w.state), cov=tile(w.cov),
                                      charge=np.tile(w.charge, 4)[:m], hit=tile(w.hit),
                                      hitcov=tile(w.hitcov))
-            bm = [kf.upload(wm, kind, width, dev) for _ in range(2)]
+            bm = [kf.upload(wm, kind, width, dev) for _ in range(4 if mult < 1 else 2)]
             ms_m = graph_time(bm, reps)
             scaling.append({"tracks": m, "ms": ms_m, "tracks_per_s": m / (ms_m * 1e-3),
                             "GBps": BYTES_PER_TRACK_P2R * m / (ms_m * 1e-3) / 1e9,
@@ -756,21 +770,24 @@ def main():
         finally:
             kf.kf_set_host_path(kf.KF_HOST_AUTO)
 
-    # pinned memory, the default path (direct: the kernel reads and writes the
-    # host arrays over the CPU-GPU link)
-    e2e_ms, h2d, d2h = time_host(True, kf.KF_HOST_AUTO)
-    e2e = {"value": shard.whole_job_throughput(w.n, 1, world, e2e_ms * 1e-3), "unit": UNIT,
-           "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-           "ms_per_step": e2e_ms, "host_memory": "pinned", "path": "direct"}
-    # context: the copy-engine pipeline on the same pinned arrays, and both
-    # paths from pageable memory
-    ms_copy = time_host(True, kf.KF_HOST_COPY)[0]
-    e2e["copy_path_value"] = w.n / (ms_copy * 1e-3)
-    try:
-        e2e["pageable_value"] = w.n / (time_host(False, kf.KF_HOST_AUTO)[0] * 1e-3)
-    except kf.KfError:
-        e2e["pageable_value"] = None
-    e2e["pageable_copy_path_value"] = w.n / (time_host(False, kf.KF_HOST_COPY)[0] * 1e-3)
+    e2e = None
+    if not args.no_e2e:
+        # pinned memory, the default path (direct: the kernel reads and writes
+        # the host arrays over the CPU-GPU link)
+        e2e_ms, h2d, d2h = time_host(True, kf.KF_HOST_AUTO)
+        e2e = {"value": shard.whole_job_throughput(w.n, 1, world, e2e_ms * 1e-3), "unit": UNIT,
+               "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+               "ms_per_step": e2e_ms, "host_memory": "pinned", "path": "direct"}
+        # context: the copy-engine pipeline on the same pinned arrays, and both
+        # paths from pageable memory
+        ms_copy = time_host(True, kf.KF_HOST_COPY)[0]
+        e2e["copy_path_value"] = w.n / (ms_copy * 1e-3)
+        try:
+            e2e["pageable_value"] = w.n / (time_host(False, kf.KF_HOST_AUTO)[0] * 1e-3)
+        except kf.KfError:
+            e2e["pageable_value"] = None
+        e2e["pageable_copy_path_value"] = w.n / (time_host(False, kf.KF_HOST_COPY)[0] * 1e-3)
+
 
     # Update variants and the compressed covariance store on the same batch
     # (context for the precision study; errors are measured by the tests).
@@ -818,7 +835,8 @@ def main():
                        "precision": "fp32 standard-form update",
                        "l2": "inputs 139 MB + outputs 104 MB per step (> 126 MB L2), "
                              "rotated over 4 buffer sets",
-                       "launch": "CUDA graph of 4 launches" if graph is not None else "eager"},
+                       "launch": (f"CUDA graph of {PER_GRAPH} launches cycling over the 4 sets"
+                                  if graph is not None else "eager")},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic,
                          "peak_source": peak_src,

@@ -86,8 +86,12 @@ template <int KIND>
 __global__ void __launch_bounds__(256) redo_pass_kernel(const __grid_constant__ StepArgs a) {
   __shared__ int32_t list[kRedoSpan];
   __shared__ int count;
-  // launched as a programmatic dependent of the step kernel: wait here until
-  // it has completed and its status marks are visible
+  // Launched as a programmatic dependent of the step kernel: wait here until
+  // it has completed and its status marks are visible.  Before that, let the
+  // next kernel on the stream be scheduled (a staged step then sets up and
+  // prefetches while this pass runs; it waits for this grid to complete
+  // before it reads or writes anything).
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
   asm volatile("griddepcontrol.wait;" ::: "memory");
   const int64_t span0 = (int64_t)blockIdx.x * kRedoSpan;
   const int cnt = gather_marked(a.status, span0, a.n, list, &count);

@@ -124,6 +124,9 @@ __global__ void __launch_bounds__(256)
     redo_compressed_kernel(const __grid_constant__ CompressedArgs a) {
   __shared__ int32_t list[kRedoSpan];
   __shared__ int count;
+  // a programmatic dependent of the step kernel, as the FP32-store redo pass
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+  asm volatile("griddepcontrol.wait;" ::: "memory");
   const int64_t span0 = (int64_t)blockIdx.x * kRedoSpan;
   const int cnt = gather_marked(a.status, span0, a.n, list, &count);
   for (int q = threadIdx.x; q < cnt; q += blockDim.x) {
@@ -240,10 +243,16 @@ extern "C" int kf_propagate_update_compressed(
   }
   if (int rc = check_cuda(cudaGetLastError(), "compressed step launch")) return rc;
   if (params->precision != KF_ADAPTIVE) return KF_OK;
-  const unsigned gr = (unsigned)((d.n + kRedoSpan - 1) / kRedoSpan);
-  if (kind == KF_P2Z)
-    redo_compressed_kernel<kP2z><<<gr, threads, 0, s>>>(a);
-  else
-    redo_compressed_kernel<kP2r><<<gr, threads, 0, s>>>(a);
-  return check_cuda(cudaGetLastError(), "compressed redo pass launch");
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)((d.n + kRedoSpan - 1) / kRedoSpan));
+  cfg.blockDim = dim3(threads);
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  const cudaError_t e = kind == KF_P2Z ? cudaLaunchKernelEx(&cfg, redo_compressed_kernel<kP2z>, a)
+                                       : cudaLaunchKernelEx(&cfg, redo_compressed_kernel<kP2r>, a);
+  return check_cuda(e, "compressed redo pass launch");
 }
