@@ -430,8 +430,11 @@ def serving_bench(args, kf, W, dev, rank):
     for t in [srv.submit(*ev_in[e], *ev_out[e]) for e in range(16)]:
         srv.wait(t, 120.0)
 
-    def serve(rate, seed):
+    def serve(rate, seed, path=kf.KF_HOST_AUTO):
+        # path: the host-path mode at submission (AUTO: these pinned events go
+        # direct, the kernel on their host arrays; COPY: through the arena)
         arrivals = np.cumsum(np.random.default_rng(seed).exponential(1.0 / rate, total))
+        kf.kf_set_host_path(path)
         srv.reset_stats()
         tickets = [None] * total
         t0 = time.perf_counter()
@@ -450,6 +453,7 @@ def serving_bench(args, kf, W, dev, rank):
         for t in tickets:
             srv.wait(t, 120.0)
         t_end = time.perf_counter()
+        kf.kf_set_host_path(kf.KF_HOST_AUTO)
         st = srv.stats()
         return arrivals, {"rate_events_per_s": rate, "tracks_per_s": tracks / (t_end - t0),
                           "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"], "max_ms": st["max_ms"],
@@ -459,6 +463,8 @@ def serving_bench(args, kf, W, dev, rank):
                                                    "out")}}
 
     runs = [serve(rate, 12 + rank + k) for k, rate in enumerate(args.serve_rates)]
+    runs_copy = [serve(rate, 12 + rank + k, kf.KF_HOST_COPY)[1]
+                 for k, rate in enumerate(args.serve_rates)]
     srv.close()
     del arena
 
@@ -494,7 +500,7 @@ def serving_bench(args, kf, W, dev, rank):
     for e in range(16):
         sync_one(e)
     results = []
-    for arrivals, served in runs:
+    for (arrivals, served), served_copy in zip(runs, runs_copy):
         lat = []
         t0 = time.perf_counter()
         for k in range(total):
@@ -509,11 +515,16 @@ def serving_bench(args, kf, W, dev, rank):
         sync = {"tracks_per_s": tracks / (t_end - t0), "p50_ms": float(np.percentile(lat, 50)),
                 "p99_ms": float(np.percentile(lat, 99)), "max_ms": float(lat[-1])}
         results.append({"rate_events_per_s": served["rate_events_per_s"],
-                         "continuous_batching": served, "per_event_sync": sync})
+                         "continuous_batching": served,
+                         "continuous_batching_copy_path": served_copy,
+                         "per_event_sync": sync})
     return {"workload": f"{total} events per rate (Poisson) cycled from 256 lognormal events "
                         f"(median 5000 tracks), {L}-layer chain", "tracks": tracks,
             "by_rate": results, "latency": "arrival to results in host memory; "
-            "server latency counted from submit (= arrival: the producer never waits)"}
+            "server latency counted from submit (= arrival: the producer never waits)",
+            "paths": "continuous_batching: pinned events go direct (the batch kernel reads and "
+                     "writes their host arrays over the CPU-GPU link); "
+                     "continuous_batching_copy_path: the same events copied through the arena"}
 
 
 def main():

@@ -230,9 +230,9 @@ int kf_p2r_propagate_update_host(const kf_params *params, kf_layout layout,
 int64_t kf_host_workspace_bytes(kf_layout layout, int64_t chunk_tracks);
 
 /*
- * kf_set_host_path -- how the host-array calls (the _host pair and
- * kf_propagate_update_host_noalloc) move data, for all later calls in this
- * process:
+ * kf_set_host_path -- how the host-array calls (the _host pair,
+ * kf_propagate_update_host_noalloc and kf_server_submit) move data, for all
+ * later calls in this process:
  *   KF_HOST_AUTO    (default) direct where every array allows it, else copy;
  *   KF_HOST_COPY    always the chunked copy path;
  *   KF_HOST_DIRECT  always direct: KF_ERR_ARG when an array is not reachable
@@ -439,6 +439,17 @@ int kf_autotune_clear(void);
  * batch.  Creating a server creates its thread, three streams and
  * max_events_in_flight + 1 CUDA events; submitting and serving allocate
  * nothing (event memory comes from the arena).
+ *
+ * Direct events: where the server's GPU reaches every array of an event in
+ * place -- page-locked memory, or any mapped host memory on a device that
+ * walks the host page tables (the host-array calls' direct path; the
+ * kf_set_host_path mode in force at submission decides) -- the batch kernel
+ * reads the event's inputs from and writes its results to the caller's
+ * arrays itself.  Such an event is ready for the next batch as soon as it is
+ * admitted and done as soon as its batch completes: no copy-in, no
+ * copy-out; the arena holds only its status marks (n bytes rounded up to
+ * 256).  Other events are copied in and out through the arena.  The results
+ * are the same either way, bit for bit.
  */
 typedef struct kf_server kf_server;
 
@@ -475,7 +486,8 @@ typedef struct {
     double  copyin_p50_ms, copyin_p99_ms;
 } kf_server_stats;
 
-/* Arena bytes one event of n tracks and L layers occupies (-1 if invalid). */
+/* Arena bytes one copied event of n tracks and L layers occupies (-1 if
+ * invalid); a direct event occupies n bytes rounded up to 256. */
 int64_t kf_server_event_bytes(int64_t n, int32_t L);
 
 /* Create a server (starts its thread).  KF_ERR_ARG for a bad config or an
@@ -486,9 +498,12 @@ int kf_server_create(const kf_server_config *cfg, kf_server **out);
  * Submit one event of n tracks.  HOST arrays, SoA per event: state [6][n],
  * cov [21][n] packed, charge [n], hits [L][3][n], hit_covs [L][6][n]; results
  * are written to state_out [6][n], cov_out [21][n] and status_out [n]
- * (status_out may be NULL).  The arrays must stay valid until the event is
- * done; page-locked memory lets the copies overlap.  Returns at once with a
- * ticket.  KF_ERR_ARG if the event can never fit the arena.
+ * (status_out may be NULL).  The arrays must stay valid, and the inputs
+ * unchanged, until the event is done; page-locked memory lets the copies
+ * overlap, or the event go direct.  Returns at once with a ticket.
+ * KF_ERR_ARG if the event can never fit the arena, if an array is pageable
+ * memory with unmapped pages or page-locked memory shorter than the event,
+ * or (under KF_HOST_DIRECT) if the event cannot go direct.
  */
 int kf_server_submit(kf_server *s, int64_t n, const float *state,
                      const float *cov, const int8_t *charge, const float *hits,

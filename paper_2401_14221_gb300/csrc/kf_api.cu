@@ -114,10 +114,22 @@ int check_device_range(const void *p, int64_t bytes, const char *name, bool *not
                      cudaGetErrorString(e));
   }
   const uintptr_t ptr = reinterpret_cast<uintptr_t>(p);
+  if (attr.type == cudaMemoryTypeHost && attr.devicePointer == nullptr) {
+    // A host thread that has made no CUDA call yet has no context bound, and
+    // page-locked memory then reports no device address: bind the thread's
+    // current device and ask again.
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaSetDevice(dev) != cudaSuccess ||
+        cudaPointerGetAttributes(&attr, p) != cudaSuccess) {
+      cudaGetLastError();
+      return set_error(KF_ERR_ARG, "%s: page-locked memory not reachable from this thread's "
+                       "device", name);
+    }
+  }
   if (attr.type == cudaMemoryTypeHost) {  // page-locked host memory
     if (attr.devicePointer != p)
-      return set_error(KF_ERR_ARG, "%s: page-locked memory whose device address differs from its "
-                       "host address", name);
+      return set_error(KF_ERR_ARG, "%s: page-locked memory whose device address (%p) differs "
+                       "from its host address (%p)", name, attr.devicePointer, p);
     PtrAttrFn fn = ptr_attr_fn();
     if (!fn) return set_error(KF_ERR_CUDA, "cuPointerGetAttribute is unavailable");
     CUdeviceptr base = 0;
@@ -149,7 +161,8 @@ int check_device_memory(const void *p, int64_t bytes, const char *name) {
   return KF_OK;
 }
 
-int host_reach(const void *p, int64_t bytes, int align, const char *name, bool *direct) {
+int host_reach(const void *p, int64_t bytes, int align, const char *name, bool *direct,
+               int dev) {
   *direct = false;
   if (!p) return set_error(KF_ERR_ARG, "%s is NULL", name);
   const bool aligned = (reinterpret_cast<uintptr_t>(p) % (uintptr_t)align) == 0;
@@ -166,8 +179,8 @@ int host_reach(const void *p, int64_t bytes, int align, const char *name, bool *
   if (!host_range_mapped(p, bytes))
     return set_error(KF_ERR_ARG, "%s: [%p, +%lld bytes) is not mapped host memory", name, p,
                      (long long)bytes);
-  int dev = 0;
-  if (int rc = check_cuda(cudaGetDevice(&dev), "cudaGetDevice")) return rc;
+  if (dev < 0)
+    if (int rc = check_cuda(cudaGetDevice(&dev), "cudaGetDevice")) return rc;
   *direct = aligned && pageable_access(dev);
   return KF_OK;
 }

@@ -61,7 +61,10 @@ int check_device_memory(const void *p, int64_t bytes, const char *name);
 // memory that is mapped over the whole range -- and `align` divides p;
 // KF_OK with *direct cleared when only the copy path can serve it; KF_ERR_ARG
 // for NULL or a range that is short or not mapped.
-int host_reach(const void *p, int64_t bytes, int align, const char *name, bool *direct);
+// `dev` is the device whose kernels would do the access (-1: the calling
+// thread's current device).
+int host_reach(const void *p, int64_t bytes, int align, const char *name, bool *direct,
+               int dev = -1);
 
 // True when [a, a+na) and [b, b+nb) overlap but do not coincide.
 inline bool partial_overlap(const void *a, int64_t na, const void *b, int64_t nb) {

@@ -16,6 +16,14 @@
 //      land marks the event done, records its latency (submit to results in
 //      host memory) and returns its slot and arena space.
 //
+// Direct events skip the copies: where the GPU reaches every array of an
+// event in place (page-locked memory, or pageable memory on a device that
+// walks the host page tables -- the host-array calls' direct path), the
+// batch kernel reads the event's inputs from and writes its results to the
+// caller's arrays over the CPU-GPU link.  Such an event is ready as soon as
+// it is admitted and done as soon as its batch completes; the arena holds
+// only its status marks.
+//
 // The track arithmetic is the chain kernel's (kf_chain.cuh), one thread per
 // track, so an event's results do not depend on what else is in its batch.
 // Streams, events and the thread are created when the server is created;
@@ -36,6 +44,7 @@
 #include "kf_chain.cuh"
 #include "kf_common.cuh"
 #include "kf_device.cuh"
+#include "kf_host.cuh"
 #include "kf_step.cuh"
 
 namespace kf {
@@ -43,9 +52,14 @@ namespace srv {
 
 constexpr int kMaxBatch = 128;
 
+// One event of a batch.  Copied events: inputs and outputs are the same
+// arena arrays (the chain runs in place).  Direct events: the caller's host
+// arrays.
 struct EventDesc {
-  float *state;
-  float *cov;
+  const float *state_in;
+  const float *cov_in;
+  float *state_out;
+  float *cov_out;
   const int8_t *charge;
   const float *hits;
   const float *hitcovs;
@@ -82,9 +96,9 @@ __global__ void __launch_bounds__(256) batch_chain_kernel(const __grid_constant_
   const ChainLoc l6{i, e.n}, l21{i, e.n}, l3{i, e.n};
   float p[6], C[21];
 #pragma unroll
-  for (int c = 0; c < 6; ++c) p[c] = e.state[l6.base + c * l6.stride];
+  for (int c = 0; c < 6; ++c) p[c] = e.state_in[l6.base + c * l6.stride];
 #pragma unroll
-  for (int k = 0; k < 21; ++k) C[k] = e.cov[l21.base + k * l21.stride];
+  for (int k = 0; k < 21; ++k) C[k] = e.cov_in[l21.base + k * l21.stride];
   const float qf = (float)__ldg(e.charge + i);
   unsigned st;
   if constexpr (VARIANT == kAdaptive) {
@@ -103,9 +117,9 @@ __global__ void __launch_bounds__(256) batch_chain_kernel(const __grid_constant_
   }
   st |= finite_status(p, C);
 #pragma unroll
-  for (int c = 0; c < 6; ++c) e.state[l6.base + c * l6.stride] = p[c];
+  for (int c = 0; c < 6; ++c) e.state_out[l6.base + c * l6.stride] = p[c];
 #pragma unroll
-  for (int k = 0; k < 21; ++k) e.cov[l21.base + k * l21.stride] = C[k];
+  for (int k = 0; k < 21; ++k) e.cov_out[l21.base + k * l21.stride] = C[k];
   if (e.status) e.status[i] = (uint8_t)st;
 }
 
@@ -113,7 +127,8 @@ __global__ void __launch_bounds__(256) batch_chain_kernel(const __grid_constant_
 // [16 r, 16 r + 16) (4,096 track slots, possibly of several events); it
 // gathers the slots whose track is marked kRedo into shared memory, then its
 // threads rerun those tracks' whole chain in double (chain_track_fp64), so
-// that warps run full.  The arena's status array is always present.
+// that warps run full.  Every event has a status array (the caller's, for a
+// direct event that gave one, else the arena's).
 constexpr int kBatchRedoBlocks = 16;
 
 __device__ __forceinline__ int batch_event_of(const BatchArgs &a, int64_t b) {
@@ -152,14 +167,14 @@ __global__ void __launch_bounds__(256) batch_redo_kernel(const __grid_constant__
     const int64_t i = idx_of[q];
     const ChainLoc l6{i, e.n}, l21{i, e.n}, l3{i, e.n};
     float p[6], C[21];
-    for (int c = 0; c < 6; ++c) p[c] = e.state[l6.base + c * l6.stride];
-    for (int k = 0; k < 21; ++k) C[k] = e.cov[l21.base + k * l21.stride];
+    for (int c = 0; c < 6; ++c) p[c] = e.state_in[l6.base + c * l6.stride];
+    for (int k = 0; k < 21; ++k) C[k] = e.cov_in[l21.base + k * l21.stride];
     const float qf = (float)e.charge[i];
     unsigned st = chain_track_fp64(p, C, qf, a.bz, a.L, a.kinds, a.pos, e.hits, 3 * e.n,
                                    e.hitcovs, 6 * e.n, l3, l6);
     st |= finite_status(p, C);
-    for (int c = 0; c < 6; ++c) e.state[l6.base + c * l6.stride] = p[c];
-    for (int k = 0; k < 21; ++k) e.cov[l21.base + k * l21.stride] = C[k];
+    for (int c = 0; c < 6; ++c) e.state_out[l6.base + c * l6.stride] = p[c];
+    for (int k = 0; k < 21; ++k) e.cov_out[l21.base + k * l21.stride] = C[k];
     e.status[i] = (uint8_t)st;
   }
 }
@@ -183,6 +198,15 @@ Layout event_layout(int64_t n, int L) {
   return l;
 }
 
+// A direct event's arena block: its status marks only.
+Layout direct_layout(int64_t n) {
+  Layout l{};
+  l.state = l.cov = l.charge = l.hits = l.hitcovs = -1;
+  l.status = 0;
+  l.bytes = align256(n);
+  return l;
+}
+
 enum class Phase { kPending, kCopying, kRunning, kReturning, kDone };
 
 struct Request {
@@ -196,6 +220,7 @@ struct Request {
   float *state_out;
   float *cov_out;
   uint8_t *status_out;
+  bool direct = false;  // the batch kernel works on the caller's arrays in place
   Phase phase = Phase::kPending;
   int64_t off = -1;  // arena offset
   Layout lay{};
@@ -332,12 +357,27 @@ bool launch_batch(kf_server *s, std::vector<Request *> &batch) {
     Request *r = batch[k];
     char *b = s->arena_base + r->off;
     EventDesc &e = a.ev[k];
-    e.state = reinterpret_cast<float *>(b + r->lay.state);
-    e.cov = reinterpret_cast<float *>(b + r->lay.cov);
-    e.charge = reinterpret_cast<const int8_t *>(b + r->lay.charge);
-    e.hits = reinterpret_cast<const float *>(b + r->lay.hits);
-    e.hitcovs = reinterpret_cast<const float *>(b + r->lay.hitcovs);
-    e.status = reinterpret_cast<uint8_t *>(b + r->lay.status);
+    if (r->direct) {
+      e.state_in = r->state;
+      e.cov_in = r->cov;
+      e.state_out = r->state_out;
+      e.cov_out = r->cov_out;
+      e.charge = r->charge;
+      e.hits = r->hits;
+      e.hitcovs = r->hitcovs;
+      e.status = r->status_out ? r->status_out : reinterpret_cast<uint8_t *>(b + r->lay.status);
+    } else {
+      float *st = reinterpret_cast<float *>(b + r->lay.state);
+      float *cv = reinterpret_cast<float *>(b + r->lay.cov);
+      e.state_in = st;
+      e.cov_in = cv;
+      e.state_out = st;
+      e.cov_out = cv;
+      e.charge = reinterpret_cast<const int8_t *>(b + r->lay.charge);
+      e.hits = reinterpret_cast<const float *>(b + r->lay.hits);
+      e.hitcovs = reinterpret_cast<const float *>(b + r->lay.hitcovs);
+      e.status = reinterpret_cast<uint8_t *>(b + r->lay.status);
+    }
     e.n = r->n;
     e.block_begin = blocks;
     blocks += (r->n + 255) / 256;
@@ -374,6 +414,28 @@ bool launch_batch(kf_server *s, std::vector<Request *> &batch) {
   return true;
 }
 
+// The event's results are in host memory: record its latency, return its
+// slot, event object and arena space, wake its waiters.
+void finish_request(kf_server *s, Request *r) {
+  r->t_done = std::chrono::steady_clock::now();
+  r->phase = Phase::kDone;
+  auto ms = [](std::chrono::steady_clock::time_point a, std::chrono::steady_clock::time_point b) {
+    return std::chrono::duration<double, std::milli>(b - a).count();
+  };
+  s->latencies_ms.push_back(ms(r->t_submit, r->t_done));
+  s->phase_ms[0].push_back(ms(r->t_submit, r->t_admit));
+  s->phase_ms[1].push_back(ms(r->t_admit, r->t_launch));
+  s->phase_ms[2].push_back(ms(r->t_launch, r->t_finished));
+  s->phase_ms[3].push_back(ms(r->t_finished, r->t_done));
+  s->phase_ms[4].push_back(ms(r->t_admit, r->t_copied));
+  s->tracks_done += r->n;
+  s->arena.release(r->off, r->lay.bytes);
+  s->event_pool.push_back(r->ev);
+  r->ev = nullptr;
+  s->in_flight -= 1;
+  s->cv_done.notify_all();
+}
+
 // One pass of the scheduler; returns true if anything moved.
 bool schedule_once(kf_server *s) {
   bool moved = false;
@@ -386,27 +448,12 @@ bool schedule_once(kf_server *s) {
       continue;
     }
     if (q != cudaSuccess) fail_locked(s, q, "server copy-out completion");
-    r->t_done = std::chrono::steady_clock::now();
-    r->phase = Phase::kDone;
-    auto ms = [](std::chrono::steady_clock::time_point a, std::chrono::steady_clock::time_point b) {
-      return std::chrono::duration<double, std::milli>(b - a).count();
-    };
-    s->latencies_ms.push_back(ms(r->t_submit, r->t_done));
-    s->phase_ms[0].push_back(ms(r->t_submit, r->t_admit));
-    s->phase_ms[1].push_back(ms(r->t_admit, r->t_launch));
-    s->phase_ms[2].push_back(ms(r->t_launch, r->t_finished));
-    s->phase_ms[3].push_back(ms(r->t_finished, r->t_done));
-    s->phase_ms[4].push_back(ms(r->t_admit, r->t_copied));
-    s->tracks_done += r->n;
-    s->arena.release(r->off, r->lay.bytes);
-    s->event_pool.push_back(r->ev);
-    r->ev = nullptr;
-    s->in_flight -= 1;
+    finish_request(s, r);
     s->returning.erase(s->returning.begin() + k);
     moved = true;
-    s->cv_done.notify_all();
   }
-  // the running batch finished: copy its events out
+  // the running batch finished: direct events are done (the kernel wrote
+  // their results to host memory), the others are copied out
   if (s->batch_in_flight) {
     const cudaError_t q = cudaEventQuery(s->batch_ev);
     if (q != cudaErrorNotReady) {
@@ -414,7 +461,9 @@ bool schedule_once(kf_server *s) {
       const auto now = std::chrono::steady_clock::now();
       for (Request *r : s->running) {
         r->t_finished = now;
-        if (start_copy_out(s, r)) {
+        if (r->direct) {
+          finish_request(s, r);
+        } else if (start_copy_out(s, r)) {
           r->phase = Phase::kReturning;
           s->returning.push_back(r);
         }
@@ -437,7 +486,12 @@ bool schedule_once(kf_server *s) {
     s->event_pool.pop_back();
     s->pending.pop_front();
     s->in_flight += 1;
-    if (!start_copy_in(s, r)) break;
+    if (r->direct) {  // nothing to copy: ready for the next batch
+      r->copied = true;
+      r->t_copied = r->t_admit;
+    } else if (!start_copy_in(s, r)) {
+      break;
+    }
     r->phase = Phase::kCopying;
     s->copying.push_back(r);
     moved = true;
@@ -559,11 +613,41 @@ extern "C" int kf_server_submit(kf_server *s, int64_t n, const float *state, con
     return set_error(KF_ERR_ARG, "an event needs 1 <= n < 2^31 tracks");
   if (!state || !cov || !charge || !hits || !hit_covs || !state_out || !cov_out)
     return set_error(KF_ERR_ARG, "a required pointer is NULL");
-  const kf::srv::Layout lay = kf::srv::event_layout(n, s->cfg.L);
+  // Direct when the host-path mode allows it and the server's device reaches
+  // every array in place (input and output may coincide, not overlap
+  // otherwise); else copied through the arena.
+  bool direct = false;
+  if (host_path_mode() != KF_HOST_COPY) {
+    const int64_t L = s->cfg.L;
+    const void *ptrs[] = {state, cov, charge, hits, hit_covs, state_out, cov_out, status_out};
+    const int64_t bytes[] = {4 * 6 * n, 4 * 21 * n, n, 4 * 3 * n * L, 4 * 6 * n * L,
+                             4 * 6 * n, 4 * 21 * n, n};
+    const int align[] = {4, 4, 1, 4, 4, 4, 4, 1};
+    const char *names[] = {"state", "cov", "charge", "hits", "hit_covs",
+                           "state_out", "cov_out", "status_out"};
+    direct = true;
+    for (int k = 0; k < 8 && direct; ++k) {
+      if (!ptrs[k]) continue;  // status_out may be NULL
+      bool reach = false;
+      if (int rc = host_reach(ptrs[k], bytes[k], align[k], names[k], &reach, s->cfg.device))
+        return rc;
+      direct = reach;
+    }
+    if (partial_overlap(state, 4 * 6 * n, state_out, 4 * 6 * n) ||
+        partial_overlap(cov, 4 * 21 * n, cov_out, 4 * 21 * n))
+      direct = false;
+    if (!direct && host_path_mode() == KF_HOST_DIRECT)
+      return set_error(KF_ERR_ARG, "KF_HOST_DIRECT: an array of the event is not reachable in "
+                                   "place from the server's device (or input and output "
+                                   "overlap without coinciding)");
+  }
+  const kf::srv::Layout lay =
+      direct ? kf::srv::direct_layout(n) : kf::srv::event_layout(n, s->cfg.L);
   if (lay.bytes > s->cfg.arena_bytes)
     return set_error(KF_ERR_ARG, "event of %lld tracks needs %lld arena bytes, the arena has %lld",
                      (long long)n, (long long)lay.bytes, (long long)s->cfg.arena_bytes);
   Request *r = new Request;
+  r->direct = direct;
   r->n = n;
   r->state = state;
   r->cov = cov;

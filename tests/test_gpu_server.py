@@ -4,8 +4,11 @@ Each event's result must be the same alone and in the mix: events run
 alone through kf_kalman_chain give the reference, then all events go
 through the server concurrently (batched with whatever else is in flight);
 the results must match bit for bit (one thread per track, same arithmetic).
-Failure paths are exercised on the host: a paused server makes a bounded
-wait time out, and an event larger than the arena is refused."""
+Events are either copied through the arena or, where the GPU reaches their
+host arrays in place, read and written there by the batch kernel (the
+direct path); both, and batches that mix them, are covered.  Failure paths
+are exercised on the host: a paused server makes a bounded wait time out,
+and an event larger than the arena is refused."""
 import threading
 import time
 
@@ -39,16 +42,25 @@ def events():
     return W.make_chain(events=len(sizes), seed=51, sizes=sizes, pool=20000)
 
 
-def event_arrays(cw, e):
+@pytest.fixture(params=[kf.KF_HOST_COPY, kf.KF_HOST_DIRECT], ids=["copy", "direct"])
+def host_path(request, dev):
+    """Events copied through the arena, or worked on in place by the kernel."""
+    kf.kf_set_host_path(request.param)
+    yield request.param
+    kf.kf_set_host_path(kf.KF_HOST_AUTO)
+
+
+def event_arrays(cw, e, pinned=True):
     lo = int(cw.event_sizes[:e].sum())
     hi = lo + int(cw.event_sizes[e])
-    pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
-    ins = (pin(cw.state[:, lo:hi]), pin(cw.cov[:, lo:hi]), pin(cw.charge[lo:hi]),
-           pin(cw.hit[:, :, lo:hi]), pin(cw.hitcov[:, :, lo:hi]))
+    pin = lambda t: t.pin_memory() if pinned else t
+    host = lambda a: pin(torch.from_numpy(np.ascontiguousarray(a)))
+    ins = (host(cw.state[:, lo:hi]), host(cw.cov[:, lo:hi]), host(cw.charge[lo:hi]),
+           host(cw.hit[:, :, lo:hi]), host(cw.hitcov[:, :, lo:hi]))
     n = hi - lo
-    outs = (torch.empty((6, n), dtype=torch.float32).pin_memory(),
-            torch.empty((21, n), dtype=torch.float32).pin_memory(),
-            torch.empty(n, dtype=torch.uint8).pin_memory())
+    outs = (pin(torch.empty((6, n), dtype=torch.float32)),
+            pin(torch.empty((21, n), dtype=torch.float32)),
+            pin(torch.empty(n, dtype=torch.uint8)))
     return lo, hi, ins, outs
 
 
@@ -70,10 +82,16 @@ def make_server(cw, dev, arena_bytes, slots=64, precision=kf.KF_FP32):
                      precision=precision)
 
 
-def test_results_alone_equal_results_in_the_mix(dev, events):
+@pytest.mark.parametrize("mode", ["copy", "direct", "mixed"])
+def test_results_alone_equal_results_in_the_mix(dev, events, mode):
+    # mixed: every other event is copied through the arena, the rest are
+    # direct, so batches hold both kinds
     cw = events
     refs = [alone(cw, e, dev) for e in range(len(cw.event_sizes))]
     srv = make_server(cw, dev, 512 << 20)
+    lock = threading.Lock()
+    path = {"copy": lambda e: kf.KF_HOST_COPY, "direct": lambda e: kf.KF_HOST_DIRECT,
+            "mixed": lambda e: kf.KF_HOST_COPY if e % 2 else kf.KF_HOST_DIRECT}[mode]
     try:
         arrays = [event_arrays(cw, e) for e in range(len(cw.event_sizes))]
         tickets = [None] * len(arrays)
@@ -81,7 +99,9 @@ def test_results_alone_equal_results_in_the_mix(dev, events):
         def submit(idx, gap):
             for e in idx:
                 _, _, ins, outs = arrays[e]
-                tickets[e] = srv.submit(*ins, *outs)
+                with lock:  # the host-path mode is process-wide
+                    kf.kf_set_host_path(path(e))
+                    tickets[e] = srv.submit(*ins, *outs)
                 time.sleep(gap * (e % 3))
         # first half: two threads submit while the server is paused, so the
         # events share batches; second half: submitted while batches run
@@ -110,11 +130,38 @@ def test_results_alone_equal_results_in_the_mix(dev, events):
             assert np.array_equal(outs[1].numpy(), ref[1])
             assert np.array_equal(outs[2].numpy(), ref[2])
     finally:
+        kf.kf_set_host_path(kf.KF_HOST_AUTO)
+        srv.close()
+
+
+def test_direct_events_in_pageable_memory(dev, events):
+    # on a device that walks the host page tables, events in ordinary
+    # (pageable) host memory take the direct path too
+    cw = events
+    srv = make_server(cw, dev, 64 << 20)
+    kf.kf_set_host_path(kf.KF_HOST_DIRECT)
+    try:
+        for e in range(0, len(cw.event_sizes), 7):
+            _, _, ins, outs = event_arrays(cw, e, pinned=False)
+            try:
+                t = srv.submit(*ins, *outs)
+            except kf.KfError as err:
+                if "not reachable" in str(err):
+                    pytest.skip("this device does not reach pageable host memory")
+                raise
+            srv.wait(t, 60.0)
+            ref = alone(cw, e, dev)
+            for a, b in zip(outs, ref):
+                assert np.array_equal(a.numpy(), b)
+        st = srv.stats()
+        assert st["copyin_p99_ms"] == 0.0 and st["out_p99_ms"] < 1.0
+    finally:
+        kf.kf_set_host_path(kf.KF_HOST_AUTO)
         srv.close()
 
 
 @pytest.mark.parametrize("precision", [kf.KF_ADAPTIVE, kf.KF_FP64])
-def test_server_results_match_the_oracle(dev, events, precision):
+def test_server_results_match_the_oracle(dev, events, precision, host_path):
     # adaptive: tracks with an ill-conditioned layer (grazing crossings) run
     # the whole chain again in double; FP64: every track in double.  Both
     # keep every track within the bounds.
@@ -143,8 +190,10 @@ def test_server_results_match_the_oracle(dev, events, precision):
 
 
 def test_admission_waits_for_arena_space(dev, events):
-    # an arena that holds about two of the largest events: the rest wait
+    # an arena that holds about two of the largest copied events: the rest
+    # wait
     cw = events
+    kf.kf_set_host_path(kf.KF_HOST_COPY)
     sizes = cw.event_sizes[:12]
     arena_bytes = 2 * kf.kf_server_event_bytes(int(sizes.max()), cw.L) + 4096
     fits = arena_bytes // kf.kf_server_event_bytes(int(sizes.min()), cw.L)
@@ -160,10 +209,11 @@ def test_admission_waits_for_arena_space(dev, events):
             ref = alone(cw, e, dev)
             assert np.array_equal(outs[0].numpy(), ref[0])
     finally:
+        kf.kf_set_host_path(kf.KF_HOST_AUTO)
         srv.close()
 
 
-def test_paused_server_wait_times_out_then_completes(dev, events):
+def test_paused_server_wait_times_out_then_completes(dev, events, host_path):
     cw = events
     srv = make_server(cw, dev, 64 << 20)
     try:
@@ -189,12 +239,19 @@ def test_paused_server_wait_times_out_then_completes(dev, events):
 
 
 def test_event_larger_than_arena_is_refused(dev, events):
+    # a copied event needs its whole arrays in the arena, a direct one only
+    # its status marks (n bytes rounded up to 256)
     cw = events
-    srv = make_server(cw, dev, 1 << 20)
-    try:
-        _, _, ins, outs = event_arrays(cw, int(np.argmax(cw.event_sizes)))
-        with pytest.raises(kf.KfError) as e:
-            srv.submit(*ins, *outs)
-        assert e.value.code == kf.KF_ERR_ARG
-    finally:
-        srv.close()
+    big = int(np.argmax(cw.event_sizes))
+    n = int(cw.event_sizes[big])
+    for path, arena_bytes in ((kf.KF_HOST_COPY, 1 << 20), (kf.KF_HOST_DIRECT, n - 256)):
+        srv = make_server(cw, dev, arena_bytes)
+        kf.kf_set_host_path(path)
+        try:
+            _, _, ins, outs = event_arrays(cw, big)
+            with pytest.raises(kf.KfError) as e:
+                srv.submit(*ins, *outs)
+            assert e.value.code == kf.KF_ERR_ARG
+        finally:
+            kf.kf_set_host_path(kf.KF_HOST_AUTO)
+            srv.close()
