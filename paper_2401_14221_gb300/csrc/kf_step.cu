@@ -18,6 +18,14 @@
 
 namespace kf {
 
+namespace staged {
+// defined with the staged step kernel's dispatch (kf_step_staged.cu)
+int sm_count(int dev, int *out);
+}  // namespace staged
+
+// CTAs per SM of the grid-stride kernel for arrays in host memory.
+constexpr int kHostGridPerSm = 1;
+
 struct Loc {
   int64_t base;
   int64_t stride;
@@ -31,10 +39,9 @@ __device__ __forceinline__ Loc locate(int64_t i, int64_t n, int32_t soa, int32_t
   return {(i >> lw) * (C * W) + (i & (W - 1)), W};
 }
 
+// Track i of a step launch (i < a.n): load, step, store.
 template <int KIND, int VARIANT>
-__global__ void __launch_bounds__(256) step_kernel(const __grid_constant__ StepArgs a) {
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= a.n) return;
+__device__ __forceinline__ void step_track(const StepArgs &a, int64_t i) {
   const Loc l6 = locate<6>(i, a.n, a.soa, a.lw);
   const Loc l21 = locate<21>(i, a.n, a.soa, a.lw);
   const Loc l3 = locate<3>(i, a.n, a.soa, a.lw);
@@ -77,6 +84,27 @@ __global__ void __launch_bounds__(256) step_kernel(const __grid_constant__ StepA
 #pragma unroll
   for (int e = 0; e < 21; ++e) __stcs(a.cov_out + l21.base + e * l21.stride, C[e]);
   if (a.status) a.status[i] = (uint8_t)st;
+}
+
+// One track per thread.
+template <int KIND, int VARIANT>
+__global__ void __launch_bounds__(256) step_kernel(const __grid_constant__ StepArgs a) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < a.n) step_track<KIND, VARIANT>(a, i);
+}
+
+// The same as a persistent grid-stride loop, for arrays in host memory: a
+// small grid whose warps are at different points of their tracks keeps both
+// directions of the CPU-GPU link busy at once, where a grid of n / 256 CTAs
+// reads in waves and then writes in waves.  Measured on GB300, 960,000 p2r
+// tracks from page-locked memory: one track per thread 0.896 ms; grid-stride
+// with 1, 2, 4 CTAs of 256 threads per SM 0.725, 0.758, 0.780 ms; half the
+// SMs 0.739 ms; 128-thread CTAs 0.736 ms.
+template <int KIND, int VARIANT>
+__global__ void __launch_bounds__(256) step_kernel_strided(const __grid_constant__ StepArgs a) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += stride)
+    step_track<KIND, VARIANT>(a, i);
 }
 
 // The redo pass of KF_ADAPTIVE: each block gathers the marked tracks of its
@@ -217,6 +245,31 @@ static int launch_step_main(int kind, int precision, const StepArgs &a, cudaStre
   }
   if (staged_ok && cfg.kernel == KF_STEP_STAGED)
     return launch_step_staged(kind, precision, a, s, cfg.ctas_per_sm);
+  if (plain_loads) {
+    int dev = 0, sms = 0;
+    if (int rc = check_cuda(cudaGetDevice(&dev), "cudaGetDevice")) return rc;
+    if (int rc = staged::sm_count(dev, &sms)) return rc;
+    const int64_t want = (a.n + 255) / 256, cap = (int64_t)kHostGridPerSm * sms;
+    const unsigned g = (unsigned)(want < cap ? want : cap);
+    if (kind == kP2z) {
+      switch (precision) {
+        case KF_FP32: step_kernel_strided<kP2z, kFP32><<<g, 256, 0, s>>>(a); break;
+        case KF_FP64_UPDATE: step_kernel_strided<kP2z, kFP64Update><<<g, 256, 0, s>>>(a); break;
+        case KF_JOSEPH: step_kernel_strided<kP2z, kJoseph><<<g, 256, 0, s>>>(a); break;
+        case KF_FP64: step_kernel_strided<kP2z, kFP64><<<g, 256, 0, s>>>(a); break;
+        default: step_kernel_strided<kP2z, kAdaptive><<<g, 256, 0, s>>>(a); break;
+      }
+    } else {
+      switch (precision) {
+        case KF_FP32: step_kernel_strided<kP2r, kFP32><<<g, 256, 0, s>>>(a); break;
+        case KF_FP64_UPDATE: step_kernel_strided<kP2r, kFP64Update><<<g, 256, 0, s>>>(a); break;
+        case KF_JOSEPH: step_kernel_strided<kP2r, kJoseph><<<g, 256, 0, s>>>(a); break;
+        case KF_FP64: step_kernel_strided<kP2r, kFP64><<<g, 256, 0, s>>>(a); break;
+        default: step_kernel_strided<kP2r, kAdaptive><<<g, 256, 0, s>>>(a); break;
+      }
+    }
+    return check_cuda(cudaGetLastError(), "host-resident step launch");
+  }
   const int threads = (cfg.threads == 128 || cfg.threads == 64) ? cfg.threads : 256;
   const int64_t blocks = (a.n + threads - 1) / threads;
   if (blocks > 0x7fffffffLL) return set_error(KF_ERR_ARG, "n too large for one launch");
