@@ -700,11 +700,24 @@ def main():
     # of one launch, graph-replayed back to back; and p2z at the p2r batch
     # size (237 algorithmic bytes per track: hit z and three hit-covariance
     # entries are not read)
-    p2z_small_us, p2z_big = None, None
+    p2z_small_us, p2z_small_isolated_us, p2z_big = None, None, None
     if not args.no_scaling:
         w_small = W.make_p2z(8192, seed=shard.rank_seed(1, rank))
         small = [kf.upload(w_small, kind, width, dev) for _ in range(2)]
         p2z_small_us = graph_time(small, 500) * 1e3
+        # and as the latency of one launch on an idle GPU: events around a
+        # single launch, synchronised before and after (median of 50)
+        lat = []
+        for k in range(55):
+            torch.cuda.synchronize()
+            a_, b_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a_.record()
+            small[k % 2].run()
+            b_.record()
+            torch.cuda.synchronize()
+            if k >= 5:
+                lat.append(a_.elapsed_time(b_) * 1e3)
+        p2z_small_isolated_us = float(np.median(lat))
         del small
         w_z = W.make_p2z(w.n, seed=shard.rank_seed(2, rank))
         bz_ = [kf.upload(w_z, kind, width, dev) for _ in range(4)]
@@ -863,6 +876,7 @@ def main():
             "spread": spread,
             "batch_scaling": scaling,
             "p2z_8192_us_per_launch": p2z_small_us,
+            "p2z_8192_isolated_latency_us": p2z_small_isolated_us,
             "p2z_960k": p2z_big,
             "sweep": sweep,
             "autotune": tuned,
