@@ -91,7 +91,7 @@ def parse():
                     help="Poisson arrival rates of the serving measurement, events/s")
     ap.add_argument("--profile-only", action="store_true",
                     help="run a few launches of one layout and exit (for ncu captures)")
-    ap.add_argument("--kind", choices=["p2r", "p2z", "chain"], default="p2r",
+    ap.add_argument("--kind", choices=["p2r", "p2z", "chain", "compressed"], default="p2r",
                     help="workload of --profile-only")
     ap.add_argument("--e2e-chunk", type=int, default=0,
                     help="tracks per pipeline chunk of the host-array call (0 = library default)")
@@ -272,7 +272,7 @@ def cpu_baseline(w):
             "single_core_sample": f"the first {m} tracks of the workload on one thread"}
 
 
-def compressed_bench(kf, W, w, dev, kind, width):
+def compressed_bench(kf, W, w, dev, kind, width, reps=100):
     """The step on the compressed covariance store (FP32 sigmas + FP16
     correlations): 193 algorithmic bytes per p2r track instead of 253."""
     import torch
@@ -298,11 +298,11 @@ def compressed_bench(kf, W, w, dev, kind, width):
     torch.cuda.synchronize()
     a, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     a.record()
-    for i in range(100):
+    for i in range(reps):
         run(bufs[i % 4])
     e.record()
     torch.cuda.synchronize()
-    ms = a.elapsed_time(e) / 100
+    ms = a.elapsed_time(e) / reps
     return {"ms": ms, "tracks_per_s": w.n / (ms * 1e-3), "bytes_per_track": 193,
             "GBps": 193 * w.n / (ms * 1e-3) / 1e9,
             "kernel": "staged (bulk copies)" if kind == kf.KF_AOSOA else "one thread per track"}
@@ -563,6 +563,13 @@ def main():
         torch.cuda.synchronize()
         print(f"profile-only: chain n={cw.n} L={cw.L}: 3 launches done")
         return 0
+    if args.profile_only and args.kind == "compressed":
+        # the p2r step on the compressed covariance store, a few launches
+        w = W.make_p2r(NEVTS, NTRKS, seed=1)
+        kind, width = layouts["aosoa32" if args.layout == "auto" else args.layout]
+        out = compressed_bench(kf, W, w, dev, kind, width, reps=5)
+        print(f"profile-only: compressed n={w.n} layout={args.layout}: {out['ms']:.4f} ms")
+        return 0
     if args.profile_only:
         w = (W.make_p2r(NEVTS, NTRKS, seed=1) if args.kind == "p2r"
              else W.make_p2z(NEVTS * NTRKS, seed=1))
@@ -700,24 +707,35 @@ def main():
     # of one launch, graph-replayed back to back; and p2z at the p2r batch
     # size (237 algorithmic bytes per track: hit z and three hit-covariance
     # entries are not read)
-    p2z_small_us, p2z_small_isolated_us, p2z_big = None, None, None
+    p2z_small_us, p2z_small_isolated_us, p2z_small_call_us, p2z_big = None, None, None, None
     if not args.no_scaling:
         w_small = W.make_p2z(8192, seed=shard.rank_seed(1, rank))
         small = [kf.upload(w_small, kind, width, dev) for _ in range(2)]
         p2z_small_us = graph_time(small, 500) * 1e3
-        # and as the latency of one launch on an idle GPU: events around a
-        # single launch, synchronised before and after (median of 50)
-        lat = []
+        # and as the latency of one launch on an otherwise idle GPU (median
+        # of 50): on the device, events around a launch that was queued behind
+        # a short sleep kernel, so that the host's call overhead is not in
+        # it; and of the whole call, the events recorded before the host
+        # makes it
+        lat, call = [], []
         for k in range(55):
             torch.cuda.synchronize()
             a_, b_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda._sleep(400000)
             a_.record()
             small[k % 2].run()
             b_.record()
             torch.cuda.synchronize()
+            c_, d_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            c_.record()
+            small[k % 2].run()
+            d_.record()
+            torch.cuda.synchronize()
             if k >= 5:
                 lat.append(a_.elapsed_time(b_) * 1e3)
+                call.append(c_.elapsed_time(d_) * 1e3)
         p2z_small_isolated_us = float(np.median(lat))
+        p2z_small_call_us = float(np.median(call))
         del small
         w_z = W.make_p2z(w.n, seed=shard.rank_seed(2, rank))
         bz_ = [kf.upload(w_z, kind, width, dev) for _ in range(4)]
@@ -877,6 +895,7 @@ def main():
             "batch_scaling": scaling,
             "p2z_8192_us_per_launch": p2z_small_us,
             "p2z_8192_isolated_latency_us": p2z_small_isolated_us,
+            "p2z_8192_call_latency_us": p2z_small_call_us,
             "p2z_960k": p2z_big,
             "sweep": sweep,
             "autotune": tuned,

@@ -39,14 +39,19 @@ __device__ __forceinline__ constexpr int od_col(int k) {
   return k - (od_row(k) * (od_row(k) - 1)) / 2;
 }
 
-// C_ii = sigma_i^2, C_ij = rho_ij sigma_i sigma_j (FP32).
+// C_ii = sigma_i^2, C_ij = rho_ij sigma_i sigma_j (FP32).  Each product is
+// rounded on its own (__fmul_rn): left as a plain multiply, the compiler may
+// fuse it with an addition of the transport that follows into one FMA, and
+// whether it does depends on the surrounding kernel, so the staged and the
+// one-thread-per-track kernels would round differently.
 __device__ __forceinline__ void decode_cov(const float (&sg)[6], const __half (&rh)[15],
                                            float (&C)[21]) {
 #pragma unroll
-  for (int c = 0; c < 6; ++c) C[tri(c, c)] = sg[c] * sg[c];
+  for (int c = 0; c < 6; ++c) C[tri(c, c)] = __fmul_rn(sg[c], sg[c]);
 #pragma unroll
   for (int k = 0; k < 15; ++k)
-    C[tri(od_row(k), od_col(k))] = __half2float(rh[k]) * sg[od_row(k)] * sg[od_col(k)];
+    C[tri(od_row(k), od_col(k))] =
+        __fmul_rn(__fmul_rn(__half2float(rh[k]), sg[od_row(k)]), sg[od_col(k)]);
 }
 
 // sigma_i = sqrt(C_ii), rho_ij = C_ij / (sigma_i sigma_j) clamped to [-1, 1]

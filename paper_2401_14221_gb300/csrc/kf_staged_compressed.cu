@@ -41,13 +41,17 @@ constexpr int kRhoB = kT * 15 * 2;
 constexpr int kHitB = kT * 3 * 4;
 constexpr int kHcB = kT * 6 * 4;
 constexpr int kStageB = kStateB + kSigB + kRhoB + kHitB + kHcB;  // 29,184 B
-constexpr int kStages = 3;
-constexpr int kSmem = kStages * (kStageB + 16);
+// Resident CTAs per SM: 3 of 2 stages each (24 compute warps per SM, at most
+// 72 registers a thread), or 2 of 3 stages.
+constexpr int kCompressedCtas = 3;
+constexpr int stages_of(int ctas) { return ctas >= 3 ? 2 : 3; }
+constexpr int smem_of(int ctas) { return stages_of(ctas) * (kStageB + 16); }
 
-template <int KIND, int VARIANT, int W>
-__global__ void __launch_bounds__(kThreads, 2)
+template <int KIND, int VARIANT, int W, int CTAS>
+__global__ void __launch_bounds__(kThreads, CTAS)
     compressed_staged_kernel(const __grid_constant__ CompressedArgs a, unsigned *err) {
   static_assert(kT % W == 0, "tile must hold whole AoSoA blocks");
+  constexpr int kStages = stages_of(CTAS);
   extern __shared__ __align__(128) unsigned char smem[];
   uint64_t *full = reinterpret_cast<uint64_t *>(smem + kStages * kStageB);
   uint64_t *empty = full + kStages;
@@ -177,7 +181,8 @@ __global__ void __launch_bounds__(kThreads, 2)
 
 template <int KIND, int VARIANT, int W>
 int launch_w(const CompressedArgs &a, cudaStream_t s, int grid, unsigned *err, int dev) {
-  auto kern = compressed_staged_kernel<KIND, VARIANT, W>;
+  constexpr int kSmem = smem_of(kCompressedCtas);
+  auto kern = compressed_staged_kernel<KIND, VARIANT, W, kCompressedCtas>;
   static std::atomic<bool> configured[64] = {};
   if (dev < 0 || dev >= 64 || !configured[dev].load(std::memory_order_acquire)) {
     if (int rc = check_cuda(
@@ -220,7 +225,7 @@ int launch_compressed_staged(int kind, int precision, const CompressedArgs &a, c
   unsigned *err = nullptr;
   if (int rc = staged::error_word(dev, &err)) return rc;
   const int64_t ntiles = (a.n + kT - 1) / kT;
-  const int64_t slots = 2LL * sms;
+  const int64_t slots = (int64_t)kCompressedCtas * sms;
   const int grid = (int)(ntiles < slots ? ntiles : slots);
   // the float-arithmetic variants (the FP64 ones stay one thread per track)
   if (kind == kP2z) {
