@@ -91,7 +91,8 @@ def parse():
                     help="Poisson arrival rates of the serving measurement, events/s")
     ap.add_argument("--profile-only", action="store_true",
                     help="run a few launches of one layout and exit (for ncu captures)")
-    ap.add_argument("--kind", choices=["p2r", "p2z", "chain", "compressed"], default="p2r",
+    ap.add_argument("--kind", choices=["p2r", "p2z", "chain", "chain_adaptive", "compressed"],
+                    default="p2r",
                     help="workload of --profile-only")
     ap.add_argument("--e2e-chunk", type=int, default=0,
                     help="tracks per pipeline chunk of the host-array call (0 = library default)")
@@ -554,14 +555,18 @@ def main():
     layouts = {"soa": (kf.KF_SOA, 0), "aosoa16": (kf.KF_AOSOA, 16), "aosoa32": (kf.KF_AOSOA, 32),
                "aosoa64": (kf.KF_AOSOA, 64), "aosoa128": (kf.KF_AOSOA, 128)}
 
-    if args.profile_only and args.kind == "chain":
-        # the fused chain on 64 events of the chain workload, a few launches
-        cw = W.make_chain(events=64, seed=7)
+    if args.profile_only and args.kind in ("chain", "chain_adaptive"):
+        # the fused chain on 64 events of the chain workload (256 for the
+        # adaptive one: its redo pass has work on the full workload), a few
+        # launches from the same start state
+        adaptive = args.kind == "chain_adaptive"
+        cw = W.make_chain(events=256 if adaptive else 64, seed=7)
         dc = kf.chain_upload(cw, kf.KF_AOSOA, 32, dev)
         for _ in range(3):
-            dc.run()
+            dc.reset()
+            dc.run(kf.KF_ADAPTIVE if adaptive else kf.KF_FP32)
         torch.cuda.synchronize()
-        print(f"profile-only: chain n={cw.n} L={cw.L}: 3 launches done")
+        print(f"profile-only: {args.kind} n={cw.n} L={cw.L}: 3 launches done")
         return 0
     if args.profile_only and args.kind == "compressed":
         # the p2r step on the compressed covariance store, a few launches
