@@ -75,3 +75,32 @@ def test_tuning_cache_text_round_trip(lib):
     assert kf.autotune_export() == line
     kf.autotune_clear()
     assert kf.autotune_export() == ""
+
+
+def test_process_wide_knobs_validate_their_argument(lib):
+    # host state only: an unknown mode is refused and leaves the setting alone
+    for fn, bad, good in ((kf.kf_set_host_path, 3, kf.KF_HOST_AUTO),
+                          (kf.kf_set_step_kernel, 3, kf.KF_STEP_AUTO),
+                          (kf.kf_set_staged_ctas_per_sm, 4, 0)):
+        with pytest.raises(kf.KfError) as e:
+            fn(bad)
+        assert e.value.code == kf.KF_ERR_ARG
+        fn(good)
+    for mode in (kf.KF_HOST_COPY, kf.KF_HOST_DIRECT, kf.KF_HOST_AUTO):
+        kf.kf_set_host_path(mode)
+
+
+def test_host_entry_argument_checks_without_gpu(lib):
+    # the host-array calls refuse bad arguments before touching any pointer
+    p = kf.make_params(3.8, precision=9)
+    rc = lib.kf_p2r_propagate_update_host(ctypes.byref(p), kf.make_layout(0, 0, 10), *[None] * 8,
+                                          0, None, None, 0, 0, None)
+    assert rc == kf.KF_ERR_ARG and "precision" in kf.kf_last_error_string()
+    rc = lib.kf_p2r_propagate_update_host(ctypes.byref(kf.make_params(3.8)),
+                                          kf.make_layout(0, 0, 10), *[None] * 8, 0, None, None,
+                                          0, 0, None)
+    assert rc == kf.KF_ERR_ARG and "NULL" in kf.kf_last_error_string()
+    rc = lib.kf_propagate_update_host_noalloc(7, ctypes.byref(kf.make_params(3.8)),
+                                              kf.make_layout(0, 0, 10), *[None] * 8, 0, None,
+                                              0, None)
+    assert rc == kf.KF_ERR_ARG
