@@ -1,6 +1,8 @@
 """The fused multi-layer chain kernel through the C ABI: against the single
 step, against L separate single-step launches, and against the FP64 oracle's
 chain on the 256-event workload (sampled)."""
+import ctypes
+
 import numpy as np
 import pytest
 import torch
@@ -118,6 +120,31 @@ def test_chain_equals_per_layer_launches_bitwise(dev, precision):
     dc.run_plain(precision)
     plain = dc.download()
     assert np.array_equal(fused[0], plain[0]) and np.array_equal(fused[1], plain[1])
+
+
+@pytest.mark.parametrize("precision", [kf.KF_FP32, kf.KF_ADAPTIVE])
+def test_chain_on_page_locked_host_arrays(dev, precision):
+    # the chain kernels reach page-locked host memory with plain loads and
+    # stores (over the CPU-GPU link): same results as on device arrays
+    cw = W.make_chain(events=4, seed=43)
+    dc = kf.chain_upload(cw, kf.KF_AOSOA, 32, dev)
+    dc.run(precision)
+    ref = dc.download()
+    pin = lambda t: t.cpu().pin_memory()
+    st, cv, q = pin(dc.state0), pin(dc.cov0), pin(dc.charge)
+    hits, hcs, status = pin(dc.hits), pin(dc.hit_covs), pin(torch.zeros_like(dc.status))
+    rc = kf.load().kf_kalman_chain(
+        ctypes.byref(kf.make_params(cw.bz, precision)), dc.layout, st.data_ptr(), cv.data_ptr(),
+        q.data_ptr(), hits.data_ptr(), hcs.data_ptr(), dc.layers, cw.L, status.data_ptr(),
+        torch.cuda.current_stream().cuda_stream)
+    assert rc == kf.KF_OK, kf.kf_last_error_string()
+    torch.cuda.synchronize()
+    dc.state.copy_(st)
+    dc.cov.copy_(cv)
+    dc.status.copy_(status)
+    got = dc.download()
+    for a, b in zip(ref, got):
+        assert np.array_equal(a, b)
 
 
 @pytest.fixture(scope="module")
