@@ -536,7 +536,9 @@ int kf_server_destroy(kf_server *s);
  * kf_set_step_kernel -- choose the single-step kernel for all later calls in
  * this process (a tuning knob; the results are the same, bit for bit):
  *   KF_STEP_AUTO    (default) the autotuner's choice where it has one, else
- *                   the staged kernel where it applies, else the direct one;
+ *                   the direct kernel for n <= 131072 (lower latency on
+ *                   small batches) and above that the staged kernel where it
+ *                   applies, else the direct one;
  *   KF_STEP_DIRECT  one thread per track with direct global loads (any layout);
  *   KF_STEP_STAGED  a persistent kernel in which a producer warp streams
  *                   tiles into shared memory with bulk asynchronous copies
@@ -568,9 +570,10 @@ int kf_set_staged_ctas_per_sm(int32_t ctas);
 #define KF_DEVERR_TIMEOUT 1u
 int kf_take_device_error(unsigned int *error_bits);
 
-/* Library version as MAJOR*10000 + MINOR*100 + PATCH (0.3.0 = 300; the
- * minor number grows with every change of a declared struct or function). */
-#define KF_VERSION 300
+/* Library version as MAJOR*10000 + MINOR*100 + PATCH (0.3.1 = 301; the
+ * minor number grows with every change of a declared struct or function, the
+ * patch number with a change of behaviour behind the same declarations). */
+#define KF_VERSION 301
 int kf_version(void);
 
 /* Message of the last KF_ERR_* returned on the calling thread ("" if none). */

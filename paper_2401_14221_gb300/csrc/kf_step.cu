@@ -26,6 +26,14 @@ int sm_count(int dev, int *out);
 // CTAs per SM of the grid-stride kernel for arrays in host memory.
 constexpr int kHostGridPerSm = 1;
 
+// Without a tuning entry, batches up to this many tracks run the
+// one-thread-per-track kernel: the staged kernel's barrier set-up and
+// pipeline fill are not repaid by so few tiles (p2z on GB300, isolated
+// launch / back to back in a graph: 8,192 tracks 6.8 / 2.3 us against
+// 8.9 / 2.8 us staged; 131,072 tracks 8.8 / 6.2 against 10.9 / 7.3 us;
+// at 960,000 the staged kernel leads, 37 against 47 us).
+constexpr int64_t kSmallBatchDirect = 131072;
+
 struct Loc {
   int64_t base;
   int64_t stride;
@@ -86,9 +94,13 @@ __device__ __forceinline__ void step_track(const StepArgs &a, int64_t i) {
   if (a.status) a.status[i] = (uint8_t)st;
 }
 
-// One track per thread.
+// One track per thread.  Launched as a programmatic dependent of the
+// previous kernel on the stream: it lets the next one be scheduled at once
+// and waits for the previous one to complete before it touches memory.
 template <int KIND, int VARIANT>
 __global__ void __launch_bounds__(256) step_kernel(const __grid_constant__ StepArgs a) {
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+  asm volatile("griddepcontrol.wait;" ::: "memory");
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i < a.n) step_track<KIND, VARIANT>(a, i);
 }
@@ -225,7 +237,8 @@ static int launch_step_main(int kind, int precision, const StepArgs &a, cudaStre
   // The staged kernel copies whole tiles of device memory with 16-byte-
   // aligned bulk copies: any AoSoA layout, SoA when n is a multiple of 4.
   const bool staged_ok = !plain_loads && (!a.soa || (a.n & 3) == 0);
-  LaunchConfig cfg{staged_ok ? KF_STEP_STAGED : KF_STEP_DIRECT, 256, 2};
+  LaunchConfig cfg{(staged_ok && a.n > kSmallBatchDirect) ? KF_STEP_STAGED : KF_STEP_DIRECT, 256,
+                   2};
   if (plain_loads) {
     // host or managed memory: the defaults above (direct, 256 threads)
   } else if (const LaunchConfig *o = thread_override()) {
@@ -273,25 +286,34 @@ static int launch_step_main(int kind, int precision, const StepArgs &a, cudaStre
   const int threads = (cfg.threads == 128 || cfg.threads == 64) ? cfg.threads : 256;
   const int64_t blocks = (a.n + threads - 1) / threads;
   if (blocks > 0x7fffffffLL) return set_error(KF_ERR_ARG, "n too large for one launch");
-  const unsigned g = (unsigned)blocks;
+  cudaLaunchConfig_t lc = {};
+  lc.gridDim = dim3((unsigned)blocks);
+  lc.blockDim = dim3((unsigned)threads);
+  lc.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  lc.attrs = attr;
+  lc.numAttrs = 1;
+  cudaError_t e;
   if (kind == kP2z) {
     switch (precision) {
-      case KF_FP32: step_kernel<kP2z, kFP32><<<g, threads, 0, s>>>(a); break;
-      case KF_FP64_UPDATE: step_kernel<kP2z, kFP64Update><<<g, threads, 0, s>>>(a); break;
-      case KF_JOSEPH: step_kernel<kP2z, kJoseph><<<g, threads, 0, s>>>(a); break;
-      case KF_FP64: step_kernel<kP2z, kFP64><<<g, threads, 0, s>>>(a); break;
-      default: step_kernel<kP2z, kAdaptive><<<g, threads, 0, s>>>(a); break;
+      case KF_FP32: e = cudaLaunchKernelEx(&lc, step_kernel<kP2z, kFP32>, a); break;
+      case KF_FP64_UPDATE: e = cudaLaunchKernelEx(&lc, step_kernel<kP2z, kFP64Update>, a); break;
+      case KF_JOSEPH: e = cudaLaunchKernelEx(&lc, step_kernel<kP2z, kJoseph>, a); break;
+      case KF_FP64: e = cudaLaunchKernelEx(&lc, step_kernel<kP2z, kFP64>, a); break;
+      default: e = cudaLaunchKernelEx(&lc, step_kernel<kP2z, kAdaptive>, a); break;
     }
   } else {
     switch (precision) {
-      case KF_FP32: step_kernel<kP2r, kFP32><<<g, threads, 0, s>>>(a); break;
-      case KF_FP64_UPDATE: step_kernel<kP2r, kFP64Update><<<g, threads, 0, s>>>(a); break;
-      case KF_JOSEPH: step_kernel<kP2r, kJoseph><<<g, threads, 0, s>>>(a); break;
-      case KF_FP64: step_kernel<kP2r, kFP64><<<g, threads, 0, s>>>(a); break;
-      default: step_kernel<kP2r, kAdaptive><<<g, threads, 0, s>>>(a); break;
+      case KF_FP32: e = cudaLaunchKernelEx(&lc, step_kernel<kP2r, kFP32>, a); break;
+      case KF_FP64_UPDATE: e = cudaLaunchKernelEx(&lc, step_kernel<kP2r, kFP64Update>, a); break;
+      case KF_JOSEPH: e = cudaLaunchKernelEx(&lc, step_kernel<kP2r, kJoseph>, a); break;
+      case KF_FP64: e = cudaLaunchKernelEx(&lc, step_kernel<kP2r, kFP64>, a); break;
+      default: e = cudaLaunchKernelEx(&lc, step_kernel<kP2r, kAdaptive>, a); break;
     }
   }
-  return check_cuda(cudaGetLastError(), kind == kP2z ? "p2z step launch" : "p2r step launch");
+  return check_cuda(e, kind == kP2z ? "p2z step launch" : "p2r step launch");
 }
 
 }  // namespace kf
