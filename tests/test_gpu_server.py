@@ -160,6 +160,26 @@ def test_direct_events_in_pageable_memory(dev, events):
         srv.close()
 
 
+def test_direct_adaptive_events_without_status(dev, events):
+    # a direct event given no status array keeps KF_ADAPTIVE's redo marks in
+    # the arena; its results equal those of the same event given one
+    cw = events
+    srv = make_server(cw, dev, 64 << 20, precision=kf.KF_ADAPTIVE)
+    kf.kf_set_host_path(kf.KF_HOST_DIRECT)
+    try:
+        for e in range(0, len(cw.event_sizes), 5):
+            _, _, ins, outs = event_arrays(cw, e)
+            _, _, _, outs2 = event_arrays(cw, e)
+            t1 = srv.submit(*ins, *outs)
+            t2 = srv.submit(*ins, outs2[0], outs2[1], None)
+            srv.wait(t1, 60.0)
+            srv.wait(t2, 60.0)
+            assert torch.equal(outs[0], outs2[0]) and torch.equal(outs[1], outs2[1])
+    finally:
+        kf.kf_set_host_path(kf.KF_HOST_AUTO)
+        srv.close()
+
+
 @pytest.mark.parametrize("precision", [kf.KF_ADAPTIVE, kf.KF_FP64])
 def test_server_results_match_the_oracle(dev, events, precision, host_path):
     # adaptive: tracks with an ill-conditioned layer (grazing crossings) run
