@@ -570,18 +570,10 @@ int kf_set_staged_ctas_per_sm(int32_t ctas);
 #define KF_DEVERR_TIMEOUT 1u
 int kf_take_device_error(unsigned int *error_bits);
 
-/*
- * kf_selftest_sincos -- s[i], c[i] = the sine and cosine of x[i] as the FP32
- * step computes them (DEVICE arrays of n floats, on `stream`).  For tests:
- * the step uses its own argument reduction and polynomials for |x| <= 1e4
- * and sincosf beyond.  KF_ERR_ARG for n < 0 or a bad pointer.
- */
-int kf_selftest_sincos(const float *x, float *s, float *c, int64_t n, void *stream);
-
-/* Library version as MAJOR*10000 + MINOR*100 + PATCH (0.4.0 = 400; the
+/* Library version as MAJOR*10000 + MINOR*100 + PATCH (0.3.1 = 301; the
  * minor number grows with every change of a declared struct or function, the
  * patch number with a change of behaviour behind the same declarations). */
-#define KF_VERSION 400
+#define KF_VERSION 301
 int kf_version(void);
 
 /* Message of the last KF_ERR_* returned on the calling thread ("" if none). */

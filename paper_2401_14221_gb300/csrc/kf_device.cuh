@@ -44,38 +44,6 @@ enum Kind : int { kP2z = 0, kP2r = 1 };
 constexpr float kRedoShrink = 1e4f;
 constexpr float kRedoGrazing = 0.2f;
 
-// sin and cos of a float argument, branch-free for |x| <= 1e4 (every angle
-// of the step: phi wrapped to (-pi, pi], theta in (0, pi), the half turning
-// angle), else sincosf.  x = k pi/2 + r with k = rint(2x / pi) and r
-// reduced in two parts (Cody and Waite's method: pi/2 split into its float
-// value and the float remainder, so k * p1 is exact for the k that occur);
-// then the Taylor series of sin and cos on |r| <= pi/4 to r^9 and r^8
-// (truncation below 2e-9) and the quadrant from k mod 4.  Within 6e-8 of
-// sincosf on |x| <= 100, and about a quarter cheaper in issue slots.
-__device__ __forceinline__ void sincos_reduced(float x, float *s, float *c) {
-  if (!(fabsf(x) <= 1e4f)) {
-    sincosf(x, s, c);
-    return;
-  }
-  const float k = rintf(x * 0.636619772367581343f);  // 2 / pi
-  float r = fmaf(-k, 1.57079637050628662109375f, x);  // float(pi / 2)
-  r = fmaf(-k, -4.37113900018624283e-8f, r);          // pi / 2 - float(pi / 2)
-  const float r2 = r * r;
-  float ps = fmaf(r2, 1.0f / 362880.0f, -1.0f / 5040.0f);
-  ps = fmaf(r2, ps, 1.0f / 120.0f);
-  ps = fmaf(r2, ps, -1.0f / 6.0f);
-  const float sr = fmaf(r * r2, ps, r);
-  float pc = fmaf(r2, 1.0f / 40320.0f, -1.0f / 720.0f);
-  pc = fmaf(r2, pc, 1.0f / 24.0f);
-  pc = fmaf(r2, pc, -0.5f);
-  const float cr = fmaf(r2, pc, 1.0f);
-  const int q = (int)k;
-  const float s0 = (q & 1) ? cr : sr;
-  const float c0 = (q & 1) ? sr : cr;
-  *s = (q & 2) ? -s0 : s0;
-  *c = ((q + 1) & 2) ? -c0 : c0;
-}
-
 // Scalar-type traits: math functions and constants for float and double.
 template <class T>
 struct Fp;
@@ -88,9 +56,7 @@ struct Fp<float> {
   static constexpr float two_pi_lo = -1.7484555314695172e-7f;  // 2 pi - float(2 pi)
   static constexpr float inv_two_pi = 0.15915494309189535f;
   static constexpr float dsinc_series = 0.25f;  // below: Taylor series for S'(h)
-  static __device__ __forceinline__ void sincos_(float x, float *s, float *c) {
-    sincos_reduced(x, s, c);
-  }
+  static __device__ __forceinline__ void sincos_(float x, float *s, float *c) { sincosf(x, s, c); }
   static __device__ __forceinline__ float fma_(float a, float b, float c) { return fmaf(a, b, c); }
   static __device__ __forceinline__ float sqrt_(float x) { return sqrtf(x); }
   static __device__ __forceinline__ float rsqrt_(float x) { return rsqrtf(x); }

@@ -141,8 +141,6 @@ def load():
     lib.kf_set_staged_ctas_per_sm.restype = ctypes.c_int
     lib.kf_set_host_path.argtypes = [ctypes.c_int32]
     lib.kf_set_host_path.restype = ctypes.c_int
-    lib.kf_selftest_sincos.argtypes = [_VP, _VP, _VP, ctypes.c_int64, _VP]
-    lib.kf_selftest_sincos.restype = ctypes.c_int
     lib.kf_take_device_error.argtypes = [ctypes.POINTER(ctypes.c_uint)]
     lib.kf_take_device_error.restype = ctypes.c_int
     lib.kf_version.restype = ctypes.c_int
@@ -361,14 +359,6 @@ KF_HOST_AUTO, KF_HOST_COPY, KF_HOST_DIRECT = 0, 1, 2
 def kf_set_host_path(mode: int) -> None:
     """C-ABI kf_set_host_path: KF_HOST_AUTO / KF_HOST_COPY / KF_HOST_DIRECT."""
     _check(load().kf_set_host_path(int(mode)))
-
-
-def kf_selftest_sincos(x: torch.Tensor, stream=None):
-    """C-ABI kf_selftest_sincos: the step's FP32 sin and cos of a device tensor."""
-    s, c = torch.empty_like(x), torch.empty_like(x)
-    _check(load().kf_selftest_sincos(_ptr(x, "x", torch.float32), _ptr(s, "s", torch.float32),
-                                     _ptr(c, "c", torch.float32), x.numel(), _stream(stream)))
-    return s, c
 
 
 def kf_take_device_error() -> int:

@@ -22,7 +22,7 @@ def test_exports_every_declared_function(lib):
 
 
 def test_version(lib):
-    assert kf.kf_version() == 400  # KF_VERSION of include/kf.h
+    assert kf.kf_version() == 301  # KF_VERSION of include/kf.h
 
 
 def _call(lib, name, params, layout):

@@ -654,36 +654,3 @@ def test_compressed_staged_equals_direct_bitwise(dev, kind, precision):
         kf.kf_set_step_kernel(kf.KF_STEP_AUTO)
     for x, y in zip(staged, direct):
         assert np.array_equal(x, y)
-
-
-# ------------------------------------------------------ device sin / cos
-
-def test_step_sincos_against_float64_and_cuda(dev):
-    # The FP32 step's own sin/cos (two-part reduction by pi/2, Taylor series
-    # on |r| <= pi/4): within 1.2e-7 of the float64 values of the same float
-    # arguments, and within 2 float ulp-of-one of CUDA's sinf/cosf, over the
-    # step's ranges (phi in (-pi, pi], theta in (0, pi), turning angles) and
-    # beyond, up to where sincosf takes over (|x| > 1e4).
-    rng = np.random.default_rng(3)
-    xs = np.concatenate([np.linspace(-np.pi, np.pi, 400001), rng.uniform(-50, 50, 200000),
-                         rng.uniform(-1e4, 1e4, 100000), rng.uniform(-1e6, 1e6, 1000),
-                         np.array([0.0, -0.0, 1e-30, np.pi / 2, np.pi, -np.pi, 3 * np.pi / 2,
-                                   1e4, -1e4, 1.0001e4])]).astype(np.float32)
-    x = torch.from_numpy(xs).to(dev)
-    s, c = kf.kf_selftest_sincos(x)
-    torch.cuda.synchronize()
-    s, c = s.cpu().numpy().astype(np.float64), c.cpu().numpy().astype(np.float64)
-    x64 = xs.astype(np.float64)
-    small = np.abs(x64) <= 1e4
-    assert np.max(np.abs(s[small] - np.sin(x64[small]))) < 1.2e-7
-    assert np.max(np.abs(c[small] - np.cos(x64[small]))) < 1.2e-7
-    # near the zeros of sin and cos (theta near pi/2 makes cos small, the
-    # p2z path divides by it) the value keeps its relative precision over
-    # the step's angles
-    for f, g in ((s, np.sin), (c, np.cos)):
-        z = (np.abs(g(x64)) < 1e-3) & (np.abs(x64) <= 100.0)
-        assert z.sum() > 10
-        assert np.all(np.abs(f[z] - g(x64[z])) <= 2e-6 * np.abs(g(x64[z])) + 1e-13)
-    ref_s, ref_c = torch.sin(x).cpu().numpy(), torch.cos(x).cpu().numpy()
-    assert np.max(np.abs(s - ref_s)) <= 2 * 2.0 ** -23 * 1.0001
-    assert np.max(np.abs(c - ref_c)) <= 2 * 2.0 ** -23 * 1.0001
