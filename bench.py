@@ -824,7 +824,11 @@ def main():
         e2e_ms, h2d, d2h = time_host(True, kf.KF_HOST_AUTO)
         e2e = {"value": shard.whole_job_throughput(w.n, 1, world, e2e_ms * 1e-3), "unit": UNIT,
                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-               "ms_per_step": e2e_ms, "host_memory": "pinned", "path": "direct"}
+               "ms_per_step": e2e_ms, "host_memory": "pinned", "path": "direct",
+               "transfer": "the step kernel loads the inputs from and stores the results to "
+                           "the pinned host arrays over the CPU-GPU link inside the timed "
+                           "region (no copy engine); copy_path_value: the same with chunked "
+                           "cudaMemcpyAsync copies"}
         # context: the copy-engine pipeline on the same pinned arrays, and both
         # paths from pageable memory
         ms_copy = time_host(True, kf.KF_HOST_COPY)[0]
