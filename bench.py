@@ -318,8 +318,39 @@ def chain_bench(args, kf, W, dev, rank):
     from paper_2401_14221_gb300 import shard
 
     cw = W.make_chain(events=256, seed=shard.rank_seed(7, rank))
-    dc = kf.chain_upload(cw, kf.KF_AOSOA, 32, dev)
     L = cw.L
+
+    def median_run(d, reps=5):
+        ms = []
+        for _ in range(reps + 1):
+            d.reset()
+            torch.cuda.synchronize()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            d.run()
+            b.record()
+            torch.cuda.synchronize()
+            ms.append(a.elapsed_time(b))
+        return sorted(ms[1:])[reps // 2]
+
+    # Layout picked by measurement: every layout, each with the library's
+    # chain autotuner (CTA size), timed on the fused chain; the fastest serves
+    # the comparison below.  SoA only when n is a multiple of 4: the per-layer
+    # launches of the comparison take each layer's hit arrays as 16-byte-
+    # aligned slices of the stacked arrays.
+    layouts = {"aosoa16": (kf.KF_AOSOA, 16), "aosoa32": (kf.KF_AOSOA, 32),
+               "aosoa64": (kf.KF_AOSOA, 64), "aosoa128": (kf.KF_AOSOA, 128)}
+    if cw.n % 4 == 0:
+        layouts["soa"] = (kf.KF_SOA, 0)
+    layout_sweep = {}
+    for lname, (lk, lw) in layouts.items():
+        d = kf.chain_upload(cw, lk, lw, dev)
+        kf.autotune_chain(d)
+        layout_sweep[lname] = median_run(d)
+        del d
+        torch.cuda.empty_cache()
+    chosen = min(layout_sweep, key=layout_sweep.get)
+    dc = kf.chain_upload(cw, *layouts[chosen], dev)
     # the library's chain autotuner picks the CTA size (served from its cache)
     tuned = kf.autotune_chain(dc)
     stream = torch.cuda.Stream()
@@ -392,7 +423,8 @@ def chain_bench(args, kf, W, dev, rank):
             "bytes_per_track": {"fused": fused_b, "plain": plain_b},
             "fused_launch": "CUDA graph" if fused_graph is not None else "eager",
             "plain_launch": "CUDA graph" if plain_graph is not None else "eager",
-            "autotune": tuned,
+            "autotune": tuned, "layout": chosen,
+            "layout_sweep_ms": layout_sweep,
             "timing": f"median of {reps} runs, CUDA events, state reset outside the timed pair"}
 
 
