@@ -91,7 +91,8 @@ def parse():
                     help="Poisson arrival rates of the serving measurement, events/s")
     ap.add_argument("--profile-only", action="store_true",
                     help="run a few launches of one layout and exit (for ncu captures)")
-    ap.add_argument("--kind", choices=["p2r", "p2z", "chain", "chain_adaptive", "compressed"],
+    ap.add_argument("--kind", choices=["p2r", "p2z", "chain", "chain_adaptive", "compressed",
+                                       "e2e"],
                     default="p2r",
                     help="workload of --profile-only")
     ap.add_argument("--e2e-chunk", type=int, default=0,
@@ -599,6 +600,17 @@ def main():
             dc.run(kf.KF_ADAPTIVE if adaptive else kf.KF_FP32)
         torch.cuda.synchronize()
         print(f"profile-only: {args.kind} n={cw.n} L={cw.L}: 3 launches done")
+        return 0
+    if args.profile_only and args.kind == "e2e":
+        # the host-array step on pinned memory (the direct path: the kernel
+        # reads and writes the host arrays), a few calls
+        w = W.make_p2r(NEVTS, NTRKS, seed=1)
+        kind, width = layouts["aosoa32" if args.layout == "auto" else args.layout]
+        hb = kf.host_upload(w, kind, width, dev, pinned=True)
+        for _ in range(3):
+            hb.run()
+        torch.cuda.synchronize()
+        print(f"profile-only: e2e n={w.n} layout={args.layout}: 3 calls done")
         return 0
     if args.profile_only and args.kind == "compressed":
         # the p2r step on the compressed covariance store, a few launches
