@@ -757,6 +757,7 @@ def main():
     # size (237 algorithmic bytes per track: hit z and three hit-covariance
     # entries are not read)
     p2z_small_us, p2z_small_isolated_us, p2z_small_call_us, p2z_big = None, None, None, None
+    p2z_small_prepared_us = None
     if not args.no_scaling:
         w_small = W.make_p2z(8192, seed=shard.rank_seed(1, rank))
         small = [kf.upload(w_small, kind, width, dev) for _ in range(2)]
@@ -766,7 +767,8 @@ def main():
         # a short sleep kernel, so that the host's call overhead is not in
         # it; and of the whole call, the events recorded before the host
         # makes it
-        lat, call = [], []
+        lat, call, prep = [], [], []
+        prepared = [b_.prepare() for b_ in small]
         for k in range(55):
             torch.cuda.synchronize()
             a_, b_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -780,11 +782,18 @@ def main():
             small[k % 2].run()
             d_.record()
             torch.cuda.synchronize()
+            e_, f_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e_.record()
+            prepared[k % 2]()
+            f_.record()
+            torch.cuda.synchronize()
             if k >= 5:
                 lat.append(a_.elapsed_time(b_) * 1e3)
                 call.append(c_.elapsed_time(d_) * 1e3)
+                prep.append(e_.elapsed_time(f_) * 1e3)
         p2z_small_isolated_us = float(np.median(lat))
         p2z_small_call_us = float(np.median(call))
+        p2z_small_prepared_us = float(np.median(prep))
         del small
         w_z = W.make_p2z(w.n, seed=shard.rank_seed(2, rank))
         bz_ = [kf.upload(w_z, kind, width, dev) for _ in range(4)]
@@ -949,6 +958,7 @@ def main():
             "p2z_8192_us_per_launch": p2z_small_us,
             "p2z_8192_isolated_latency_us": p2z_small_isolated_us,
             "p2z_8192_call_latency_us": p2z_small_call_us,
+            "p2z_8192_prepared_call_latency_us": p2z_small_prepared_us,
             "p2z_960k": p2z_big,
             "sweep": sweep,
             "autotune": tuned,

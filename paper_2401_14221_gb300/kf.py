@@ -274,6 +274,40 @@ KF_P2Z, KF_P2R = 0, 1
 KF_NOALLOC_MAX_CHUNK = 32768
 
 
+class PreparedStep:
+    """kf_p2z_propagate_update / kf_p2r_propagate_update with the arguments
+    checked and marshalled once; each call launches the step again on the
+    same arrays, on the given stream or the current one.  The tensors are
+    kept referenced for the object's lifetime and must not be resized.  For
+    loops over small batches, where the plain wrapper's per-call checks and
+    conversions cost several times the C call itself."""
+
+    def __init__(self, kind, params, layout, state_in, cov_in, state_out, cov_out, charge, hit,
+                 hit_cov, surf, surf_per_track=0, status=None):
+        lib = load()
+        self._fn = lib.kf_p2z_propagate_update if kind == KF_P2Z else lib.kf_p2r_propagate_update
+        f32, i8, u8 = torch.float32, torch.int8, torch.uint8
+        self._params = params
+        self._keep = (state_in, cov_in, state_out, cov_out, charge, hit, hit_cov, surf, status)
+        self._args = (ctypes.byref(params), layout,
+                      _ptr(state_in, "state_in", f32), _ptr(cov_in, "cov_in", f32),
+                      _ptr(state_out, "state_out", f32), _ptr(cov_out, "cov_out", f32),
+                      _ptr(charge, "charge", i8), _ptr(hit, "hit", f32),
+                      _ptr(hit_cov, "hit_cov", f32), _ptr(surf, "surf", f32),
+                      int(surf_per_track), _ptr(status, "status", u8))
+        self._dev = state_in.device.index if state_in.device.index is not None else 0
+        self._raw = getattr(torch._C, "_cuda_getCurrentRawStream", None)
+
+    def __call__(self, stream=None):
+        if stream is None:
+            s = self._raw(self._dev) if self._raw is not None else _stream(None)
+        else:
+            s = _stream(stream)
+        rc = self._fn(*self._args, s)
+        if rc != KF_OK:
+            _check(rc)
+
+
 def kf_propagate_update_host_noalloc(kind, params, layout, state_in, cov_in, state_out, cov_out,
                                      charge, hit, hit_cov, surf, surf_per_track=0, status=None,
                                      chunk_tracks=0, stream=None):
@@ -394,6 +428,13 @@ class DeviceBatch:
     surf: torch.Tensor
     status: torch.Tensor
     bz: float
+
+    def prepare(self, precision: int = KF_FP32) -> PreparedStep:
+        """A PreparedStep on this batch's current tensors (out of place)."""
+        return PreparedStep(KF_P2Z if self.kind == W.P2Z else KF_P2R,
+                            make_params(self.bz, precision), self.layout, self.state_in,
+                            self.cov_in, self.state_out, self.cov_out, self.charge, self.hit,
+                            self.hit_cov, self.surf, int(self.surf.numel() > 1), self.status)
 
     def run(self, precision: int = KF_FP32, stream=None, in_place: bool = False):
         fn = kf_p2z_propagate_update if self.kind == W.P2Z else kf_p2r_propagate_update

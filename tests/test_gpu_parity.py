@@ -654,3 +654,28 @@ def test_compressed_staged_equals_direct_bitwise(dev, kind, precision):
         kf.kf_set_step_kernel(kf.KF_STEP_AUTO)
     for x, y in zip(staged, direct):
         assert np.array_equal(x, y)
+
+
+def test_prepared_step_equals_the_plain_call(dev):
+    # the binding's prepared call marshals the arguments once; the launches
+    # are the same calls, so the results are the same bits, on the current
+    # stream and on another one
+    w = W.make_p2z(8192, seed=1)
+    b = kf.upload(w, kf.KF_AOSOA, 32, dev)
+    b.run()
+    torch.cuda.synchronize()
+    ref = b.download()
+    b.state_out.fill_(float("nan"))
+    b.cov_out.fill_(float("nan"))
+    step = b.prepare()
+    step()
+    torch.cuda.synchronize()
+    for x, y in zip(ref, b.download()):
+        assert np.array_equal(x, y)
+    b.state_out.fill_(float("nan"))
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        step(stream=s)
+    s.synchronize()
+    for x, y in zip(ref, b.download()):
+        assert np.array_equal(x, y)
