@@ -104,6 +104,13 @@ def workload_name():
     return f"p2r single step, {NEVTS} events x {NTRKS} tracks, r={RADIUS:g} cm, Bz=3.8 T"
 
 
+def workload_config(n):
+    """The workload, the same for both arms (what is timed, not how)."""
+    return {"workload": workload_name(), "tracks": n,
+            "l2": "inputs larger than L2: per step 139 MB of inputs and 104 MB of outputs "
+                  "against the GPU's 126 MB L2"}
+
+
 def measured_hbm_peak():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -230,8 +237,9 @@ def reference_arm(args, rank, world):
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic", "config": {"workload": workload_name(), "tracks": w.n},
+        "data": "synthetic", "config": workload_config(w.n),
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "cpu_model": cpu_model(),
                          "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
@@ -240,6 +248,28 @@ def reference_arm(args, rank, world):
 
 
 # ---------------------------------------------------------------- kf arm
+
+def cpu_model() -> str:
+    """The host CPU's model name (lscpu, else /proc/cpuinfo), for the record."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        fields = dict(line.split(":", 1) for line in out.splitlines() if ":" in line)
+        fields = {k.strip(): v.strip() for k, v in fields.items()}
+        name = fields.get("Model name") or fields.get("BIOS Model name")
+        if name:
+            vendor = fields.get("Vendor ID", "")
+            return f"{vendor} {name}".strip()
+    except (OSError, subprocess.SubprocessError, ValueError):
+        pass
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.lower().startswith(("model name", "cpu part", "hardware")):
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return "unknown"
+
 
 def cpu_baseline(w):
     """The oracle timed on this host's cores over passes of the workload."""
@@ -268,6 +298,7 @@ def cpu_baseline(w):
                       threads=1)
     one = m / (time.perf_counter() - t1)
     return {"value": passes * w.n / el, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "cpu_model": cpu_model(),
             "sample": f"{passes} full pass(es) over the {w.n}-track workload, "
                       f"{cpu_s:.1f} s CPU time",
             "single_core_value": one,
@@ -701,32 +732,53 @@ def main():
         kf.kf_set_step_kernel(kf.KF_STEP_AUTO)
         tuned = kf.autotune_step(sets[0])
 
-    # Capture PER_GRAPH launches cycling over the buffer sets in a CUDA
-    # graph; replay it.
+    # Every timed launch is a graph replay: a CUDA graph of exactly k launches
+    # cycling over the buffer sets (captured once per k, outside the timed
+    # region), so that the timed region has one graph boundary however many
+    # steps are asked for.  Beyond MAX_GRAPH launches, graphs of PER_GRAPH
+    # launches are replayed, plus one graph of the remainder.
+    MAX_GRAPH = 1024
     stream = torch.cuda.Stream()
-    graph = None
+    graphs = {}
+    graph_ok = True
+    with torch.cuda.stream(stream):
+        for s in sets:
+            s.run(stream=stream)
+    torch.cuda.synchronize()
+
+    def graph_of(k):
+        if k not in graphs:
+            g = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(g, stream=stream):
+                for i in range(k):
+                    sets[i % len(sets)].run()
+            torch.cuda.synchronize()
+            graphs[k] = g
+        return graphs[k]
+
+    def plan(k):
+        # the graphs that make up k launches, captured before any timing
+        if k <= 0:
+            return []
+        if k <= MAX_GRAPH:
+            return [graph_of(k)]
+        reps, rest = divmod(k, PER_GRAPH)
+        return [graph_of(PER_GRAPH)] * reps + ([graph_of(rest)] if rest else [])
+
     try:
-        with torch.cuda.stream(stream):
-            for s in sets:
-                s.run(stream=stream)
-        torch.cuda.synchronize()
-        graph = torch.cuda.CUDAGraph()
-        with torch.cuda.graph(graph, stream=stream):
-            for k in range(PER_GRAPH):
-                sets[k % len(sets)].run()
+        # capture, then replay every graph once: a graph's first launch also
+        # uploads it to the device, which must not land in the timed region
+        for g in set(plan(args.steps) + plan(max(args.warmup, 3))):
+            g.replay()
         torch.cuda.synchronize()
     except Exception as e:  # capture unsupported: eager launches
         print(f"# CUDA graph capture failed ({e}); timing eager launches", file=sys.stderr)
-        graph = None
-
-    reps_per_replay = PER_GRAPH if graph is not None else 1
+        graph_ok = False
 
     def run_steps(k):
-        if graph is not None:
-            for _ in range(k // reps_per_replay):
-                graph.replay()
-            for i in range(k % reps_per_replay):
-                sets[i % len(sets)].run()
+        if graph_ok:
+            for g in plan(k):
+                g.replay()
         else:
             for i in range(k):
                 sets[i % len(sets)].run()
@@ -803,18 +855,18 @@ def main():
                    "bytes_per_track": BYTES_PER_TRACK_P2Z}
         del bz_, w_z
 
-    # Spread: ten timed repeats of a tenth of the steps each.
+    # Spread: ten timed repeats of the same timed region (the same K graph-
+    # replayed launches), so that its mean and sd describe the headline.
     reps = []
-    kr = max(args.steps // 10, 4)
     for _ in range(10):
         r0, r1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         r0.record()
-        run_steps(kr)
+        run_steps(args.steps)
         r1.record()
         torch.cuda.synchronize()
-        reps.append(r0.elapsed_time(r1) / kr)
+        reps.append(r0.elapsed_time(r1) / args.steps)
     reps_sorted = sorted(reps)
-    spread = {"repeats": 10, "steps_each": kr,
+    spread = {"repeats": 10, "steps_each": args.steps,
               "ms_per_step_mean": sum(reps) / 10,
               "ms_per_step_sd": (sum((x - sum(reps) / 10) ** 2 for x in reps) / 9) ** 0.5,
               "ms_per_step_p50": 0.5 * (reps_sorted[4] + reps_sorted[5])}
@@ -933,14 +985,18 @@ def main():
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic",
-            "config": {"workload": workload_name(), "tracks": w.n, "layout": chosen,
-                       "step_kernel": (f"{tuned['step_kernel']} (autotuned: {tuned})"
-                                       if tuned else chosen_kernel),
-                       "precision": "fp32 standard-form update",
-                       "l2": "inputs 139 MB + outputs 104 MB per step (> 126 MB L2), "
-                             "rotated over 4 buffer sets",
-                       "launch": (f"CUDA graph of {PER_GRAPH} launches cycling over the 4 sets"
-                                  if graph is not None else "eager")},
+            "config": workload_config(w.n),
+            "setup": {"layout": chosen,
+                      "step_kernel": (f"{tuned['step_kernel']} (autotuned: {tuned})"
+                                      if tuned else chosen_kernel),
+                      "precision": "fp32 standard-form update",
+                      "buffers": "4 buffer sets rotated, so no step reads what the previous "
+                                 "one left in L2",
+                      "launch": ((f"one CUDA graph of the {args.steps} timed launches cycling "
+                                  "over the 4 sets" if args.steps <= MAX_GRAPH else
+                                  f"CUDA graphs of {PER_GRAPH} launches and one of the "
+                                  "remainder, cycling over the 4 sets")
+                                 if graph_ok else "eager")},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic,
                          "peak_source": peak_src,

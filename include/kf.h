@@ -350,11 +350,16 @@ int kf_kalman_chain(const kf_params *params, kf_layout layout, float *state,
  * where every array is reachable in place the kernel works on the caller's
  * arrays and the staging buffer is not used, except as the redo marks of
  * KF_ADAPTIVE without a status array (n <= KF_NOALLOC_STAGING_BYTES; larger
- * such calls take the copy path).
+ * such calls take the copy path under KF_HOST_AUTO and are refused with
+ * KF_ERR_ARG under KF_HOST_DIRECT).  Outputs that partially overlap the
+ * inputs (not exactly in place) are refused with KF_ERR_ARG.
  *
  * Set-up: the first call on a device looks up the device address of the
- * staging buffer with that device current (cudaGetSymbolAddress).  Make that
- * first call before any stream capture.
+ * staging buffer with that device current (cudaGetSymbolAddress) and keeps
+ * it for the life of the process.  Make that first call before any stream
+ * capture.  cudaDeviceReset is not supported while the library is in use:
+ * the library keeps device addresses (this buffer's, the device error
+ * word's) that a reset invalidates.
  * Sharing: every call on a device uses the same staging buffer, which keeps
  * the last call's contents (nothing in it needs to start at zero).  Calls
  * whose work overlaps on the GPU -- on different streams, or from different
@@ -562,6 +567,24 @@ int kf_set_step_kernel(int32_t mode);
 int kf_set_staged_ctas_per_sm(int32_t ctas);
 
 /*
+ * kf_set_device_wait_limit -- how long the compute warps of the staged
+ * kernels (KF_STEP_STAGED and the compressed store's staged kernel) wait for
+ * a tile before they give up, in polls of the tile's barrier (each poll
+ * backs off by about 0.1 us): 0 .. 16,777,216, or -1 for the default
+ * (16,777,216: seconds, far beyond any healthy wait, which lasts
+ * microseconds).  A wait that runs out sets KF_DEVERR_TIMEOUT in the device
+ * error word (kf_take_device_error); that CTA then stops, lets the copies it
+ * has in flight land and exits, so the call returns with its results
+ * incomplete and the GPU context stays usable.  A limit of 0 makes every
+ * such wait give up at once: every staged launch then reports
+ * KF_DEVERR_TIMEOUT, which exercises the error path.  The producer warp's
+ * own waits keep the default limit.  Process-wide, read at each launch;
+ * results of launches that do not time out are unchanged.  Returns
+ * KF_ERR_ARG outside the range.
+ */
+int kf_set_device_wait_limit(int64_t polls);
+
+/*
  * kf_take_device_error -- read and clear the library's device error word
  * (synchronous).  Kernels that wait on barriers bound every wait; a wait
  * that gives up sets KF_DEVERR_TIMEOUT here and the kernel ends early, so
@@ -573,7 +596,7 @@ int kf_take_device_error(unsigned int *error_bits);
 /* Library version as MAJOR*10000 + MINOR*100 + PATCH (0.3.1 = 301; the
  * minor number grows with every change of a declared struct or function, the
  * patch number with a change of behaviour behind the same declarations). */
-#define KF_VERSION 301
+#define KF_VERSION 400
 int kf_version(void);
 
 /* Message of the last KF_ERR_* returned on the calling thread ("" if none). */

@@ -127,11 +127,23 @@ def compare(g_state, g_cov, g_status, o_state, o_cov, o_status,
     rep["ok"] = bool(status_equal and rep["param"]["max"] <= tol_param
                      and rep["cov"]["max"] <= tol_cov)
     if not rep["ok"] and len(o_status):
-        # the worst tracks, to make a failure readable
+        # the worst tracks and the status mismatches, to make a failure
+        # readable (and recordable) on its own
+        g_state = np.asarray(g_state)
+        g_cov = np.asarray(g_cov)
         tp = int(np.argmax(pe.max(axis=1)))
         tc = int(np.argmax(ce.max(axis=1)))
-        rep["worst_param"] = {"track": tp, "err": pe[tp].tolist(), "gpu": np.asarray(g_state)[tp].tolist(),
-                              "oracle": np.asarray(o_state)[tp].tolist()}
-        rep["worst_cov"] = {"track": tc, "err": ce[tc].tolist()}
-        rep["status_mismatch_tracks"] = np.nonzero(g_status != o_status)[0][:10].tolist()
+        ec = int(np.argmax(ce[tc]))
+        rep["worst_param"] = {"track": tp, "component": int(np.argmax(pe[tp])),
+                              "err": pe[tp].tolist(), "gpu": g_state[tp].tolist(),
+                              "oracle": np.asarray(o_state)[tp].tolist(),
+                              "status_gpu": int(g_status[tp]), "status_oracle": int(o_status[tp])}
+        rep["worst_cov"] = {"track": tc, "element": ec, "err": ce[tc].tolist(),
+                            "gpu": g_cov[tc].tolist(), "oracle": np.asarray(o_cov)[tc].tolist(),
+                            "status_gpu": int(g_status[tc]), "status_oracle": int(o_status[tc])}
+        bad = np.nonzero(g_status != o_status)[0][:10]
+        rep["status_mismatch_tracks"] = bad.tolist()
+        rep["status_mismatch_values"] = [[int(g_status[t]), int(o_status[t])] for t in bad]
+        rep["tracks_over_bound"] = int(np.sum((pe.max(axis=1) > tol_param)
+                                              | (ce.max(axis=1) > tol_cov)))
     return rep

@@ -216,6 +216,14 @@ int run_host(int kind, const kf_params *params, kf_layout layout, const float *s
       return rc;
     if (taken) return KF_OK;
   }
+  // Chunks are copied back while later chunks are still to be copied in:
+  // outputs that partially overlap the inputs would overwrite inputs not yet
+  // read (in place, exactly coinciding, is safe).
+  {
+    const int64_t b6 = 4 * layout_floats(d, 6), b21 = 4 * layout_floats(d, 21);
+    if (partial_overlap(state_in, b6, state_out, b6) || partial_overlap(cov_in, b21, cov_out, b21))
+      return set_error(KF_ERR_ARG, "input and output overlap without coinciding");
+  }
   const int64_t chunk = effective_chunk(d, chunk_tracks);
   const Slot sl = slot_layout(chunk);
   if (workspace_bytes < 2 * sl.bytes)

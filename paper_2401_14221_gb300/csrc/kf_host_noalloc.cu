@@ -157,6 +157,15 @@ extern "C" int kf_propagate_update_host_noalloc(int32_t kind, const kf_params *p
     if (taken) return KF_OK;
   }
 
+  // Chunk c's outputs are copied back before chunk c + 1's inputs are copied
+  // in: outputs that partially overlap the inputs would overwrite inputs not
+  // yet read (in place, exactly coinciding, is safe).
+  {
+    const int64_t b6 = 4 * layout_floats(d, 6), b21 = 4 * layout_floats(d, 21);
+    if (partial_overlap(state_in, b6, state_out, b6) || partial_overlap(cov_in, b21, cov_out, b21))
+      return set_error(KF_ERR_ARG, "input and output overlap without coinciding");
+  }
+
   // Chunk: the requested size (default: the capacity), a whole number of
   // AoSoA blocks, never more than the staged layout holds.
   const int64_t W = d.soa ? 1 : (int64_t(1) << d.lw);

@@ -20,6 +20,7 @@ namespace staged {
 // defined with the staged step kernel's dispatch (kf_step_staged.cu)
 int sm_count(int dev, int *out);
 int error_word(int dev, unsigned **out);
+uint32_t device_wait_polls();
 }  // namespace staged
 
 namespace {
@@ -49,7 +50,8 @@ constexpr int smem_of(int ctas) { return stages_of(ctas) * (kStageB + 16); }
 
 template <int KIND, int VARIANT, int W, int CTAS>
 __global__ void __launch_bounds__(kThreads, CTAS)
-    compressed_staged_kernel(const __grid_constant__ CompressedArgs a, unsigned *err) {
+    compressed_staged_kernel(const __grid_constant__ CompressedArgs a, unsigned *err,
+                             uint32_t wait_polls) {
   static_assert(kT % W == 0, "tile must hold whole AoSoA blocks");
   constexpr int kStages = stages_of(CTAS);
   extern __shared__ __align__(128) unsigned char smem[];
@@ -59,8 +61,12 @@ __global__ void __launch_bounds__(kThreads, CTAS)
   const int lane = threadIdx.x & 31;
   const Schedule sch = staged::make_schedule<W>(a.n, gridDim.x);
   const int64_t ntiles = sch.tiles_of(blockIdx.x);
+  // raised when a warp of this CTA gives up a bounded wait (the pipeline
+  // then stops and drains, as in the FP32-store kernel)
+  __shared__ int abort_flag;
 
   if (threadIdx.x == 0) {
+    abort_flag = 0;
     for (int s = 0; s < kStages; ++s) {
       mbar_init(&full[s], 1);
       mbar_init(&empty[s], kComputeWarps);
@@ -95,7 +101,8 @@ __global__ void __launch_bounds__(kThreads, CTAS)
       for (int64_t k = 0; k < ntiles; ++k) {
         const int s = (int)(k % kStages);
         const uint32_t ph = (uint32_t)(k / kStages) & 1u;
-        if (k >= kStages && !mbar_wait(&empty[s], ph ^ 1u, err)) break;
+        if (k >= kStages && !mbar_wait(&empty[s], ph ^ 1u, err, staged::kMaxPolls, &abort_flag))
+          break;
         int64_t first, m;
         sch.tile(k, blockIdx.x, a.n, &first, &m);
         const uint32_t cols = (uint32_t)(((m + W - 1) / W) * W);  // whole blocks
@@ -127,7 +134,7 @@ __global__ void __launch_bounds__(kThreads, CTAS)
     const bool live = il < m;
     const float qf = live ? (float)__ldg(a.charge + i) : 1.0f;
     const float surf = __ldg(a.surf + ((a.surf_per_track && live) ? i : 0));
-    if (!mbar_wait(&full[s], ph, err)) break;
+    if (!mbar_wait(&full[s], ph, err, wait_polls, &abort_flag)) break;
 
     const unsigned char *st = smem + s * kStageB;
     const float *sst = reinterpret_cast<const float *>(st);
@@ -201,7 +208,8 @@ int launch_w(const CompressedArgs &a, cudaStream_t s, int grid, unsigned *err, i
   attr[0].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  return check_cuda(cudaLaunchKernelEx(&cfg, kern, a, err), "compressed staged launch");
+  return check_cuda(cudaLaunchKernelEx(&cfg, kern, a, err, staged::device_wait_polls()),
+                    "compressed staged launch");
 }
 
 template <int KIND, int VARIANT>

@@ -26,6 +26,9 @@ struct StepArgs {
   float bz;
   int32_t surf_per_track;
   unsigned *err = nullptr;  // device error word (set by the staged launcher)
+  // Polls of a staged-pipeline barrier by a compute warp before it gives up
+  // (set by the staged launcher from kf_set_device_wait_limit).
+  uint32_t wait_polls = 0;
 };
 
 #ifdef __CUDACC__

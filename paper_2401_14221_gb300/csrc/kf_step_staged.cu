@@ -18,6 +18,12 @@ namespace staged {
 std::mutex g_sm_mu;
 int g_sm_count[64] = {};
 
+// Polls of a pipeline barrier by a compute warp before it gives up
+// (kf_set_device_wait_limit).
+std::atomic<uint32_t> g_wait_polls{kMaxPolls};
+
+uint32_t device_wait_polls() { return g_wait_polls.load(std::memory_order_relaxed); }
+
 // Device address of g_device_error, looked up once per device.
 std::atomic<unsigned *> g_err_addr[64] = {};
 
@@ -73,6 +79,7 @@ int launch_step_staged(int kind, int precision, const StepArgs &a, cudaStream_t 
   const int grid = (int)(ntiles < slots ? ntiles : slots);
   StepArgs b = a;
   if (int rc = error_word(dev, &b.err)) return rc;
+  b.wait_polls = device_wait_polls();
   const bool f64 = precision == KF_FP64_UPDATE || precision == KF_FP64;
   if (kind == kP2z)
     return f64 ? launch_staged_p2z_f64(precision, b, s, grid, dev, ctas)
@@ -82,6 +89,16 @@ int launch_step_staged(int kind, int precision, const StepArgs &a, cudaStream_t 
 }
 
 }  // namespace kf
+
+extern "C" int kf_set_device_wait_limit(int64_t polls) {
+  kf::clear_error();
+  if (polls < -1 || polls > (int64_t)kf::staged::kMaxPolls)
+    return kf::set_error(KF_ERR_ARG, "wait limit %lld is not -1 or 0..%u", (long long)polls,
+                         kf::staged::kMaxPolls);
+  kf::staged::g_wait_polls.store(polls < 0 ? kf::staged::kMaxPolls : (uint32_t)polls,
+                                 std::memory_order_relaxed);
+  return KF_OK;
+}
 
 extern "C" int kf_take_device_error(unsigned int *error_bits) {
   kf::clear_error();

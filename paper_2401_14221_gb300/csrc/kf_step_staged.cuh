@@ -102,14 +102,23 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
   return ok != 0;
 }
 
-// Wait for the phase with the given parity to complete; false on timeout
-// (KF_DEVERR_TIMEOUT is then OR-ed into the library's device error word).
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, unsigned *err) {
-  for (uint32_t it = 0; it < kMaxPolls; ++it) {
+// Wait for the phase with the given parity to complete, polling at most
+// `limit` times (with back-off); false when it gives up.  A wait that runs
+// out ORs KF_DEVERR_TIMEOUT into the library's device error word and, when
+// the CTA has an abort flag, raises it; a wait given an abort flag also
+// gives up (without a second error bit) as soon as another warp of the CTA
+// has raised it, so one warp's timeout ends the whole CTA's pipeline in
+// microseconds instead of every warp polling to its own limit.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, unsigned *err,
+                                          uint32_t limit = kMaxPolls,
+                                          volatile int *abort = nullptr) {
+  for (uint32_t it = 0; it < limit; ++it) {
     if (mbar_try_wait(bar, parity)) return true;
+    if (abort && *abort) return false;
     if (it > 32) __nanosleep(128);
   }
   if (err) atomicOr(err, (unsigned)KF_DEVERR_TIMEOUT);
+  if (abort) *abort = 1;
   return false;
 }
 
@@ -194,8 +203,13 @@ __global__ void __launch_bounds__(kThreads, CTAS)
   const int lane = threadIdx.x & 31;
   const Schedule sch = make_schedule<GR>(a.n, gridDim.x);
   const int64_t ntiles = sch.tiles_of(blockIdx.x);
+  // Raised when a warp of this CTA gives up a bounded wait: the compute
+  // warps stop, and the producer stops issuing copies and drains the ones
+  // in flight before the CTA exits.
+  __shared__ int abort_flag;
 
   if (threadIdx.x == 0) {
+    abort_flag = 0;
     for (int s = 0; s < kStages; ++s) {
       mbar_init(&full[s], 1);
       mbar_init(&empty[s], kComputeWarps);
@@ -240,7 +254,7 @@ __global__ void __launch_bounds__(kThreads, CTAS)
       for (int64_t k = 0; k < ntiles; ++k) {
         const int s = (int)(k % kStages);
         const uint32_t ph = (uint32_t)(k / kStages) & 1u;
-        if (k >= kStages && !mbar_wait(&empty[s], ph ^ 1u, a.err)) break;
+        if (k >= kStages && !mbar_wait(&empty[s], ph ^ 1u, a.err, kMaxPolls, &abort_flag)) break;
         int64_t first, m;
         sch.tile(k, blockIdx.x, a.n, &first, &m);
         const uint32_t cols = (uint32_t)(((m + GR - 1) / GR) * GR);  // whole blocks
@@ -282,7 +296,9 @@ __global__ void __launch_bounds__(kThreads, CTAS)
         issued = k + 1;
       }
       // No copy may still be writing this CTA's shared memory when it exits
-      // (the compute warps have normally consumed them all already).
+      // (the compute warps have normally consumed them all already; after an
+      // abort they have not, and these waits, at the full limit and deaf to
+      // the abort flag, let the copies land).
       for (int64_t k = issued > kStages ? issued - kStages : 0; k < issued; ++k)
         if (!mbar_wait(&full[k % kStages], (uint32_t)(k / kStages) & 1u, a.err)) break;
     }
@@ -313,7 +329,7 @@ __global__ void __launch_bounds__(kThreads, CTAS)
     const bool live = il < m;
     const float qf = qf_next, surf = surf_next;
     if (k + 1 < ntiles) fetch(k + 1, qf_next, surf_next);
-    if (!mbar_wait(&full[s], ph, a.err)) break;
+    if (!mbar_wait(&full[s], ph, a.err, a.wait_polls, &abort_flag)) break;
 
     const float *sst = reinterpret_cast<const float *>(smem + s * kStageB);
     const float *scv = sst + kT * 6;

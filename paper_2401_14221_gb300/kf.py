@@ -141,6 +141,8 @@ def load():
     lib.kf_set_staged_ctas_per_sm.restype = ctypes.c_int
     lib.kf_set_host_path.argtypes = [ctypes.c_int32]
     lib.kf_set_host_path.restype = ctypes.c_int
+    lib.kf_set_device_wait_limit.argtypes = [ctypes.c_int64]
+    lib.kf_set_device_wait_limit.restype = ctypes.c_int
     lib.kf_take_device_error.argtypes = [ctypes.POINTER(ctypes.c_uint)]
     lib.kf_take_device_error.restype = ctypes.c_int
     lib.kf_version.restype = ctypes.c_int
@@ -393,6 +395,12 @@ KF_HOST_AUTO, KF_HOST_COPY, KF_HOST_DIRECT = 0, 1, 2
 def kf_set_host_path(mode: int) -> None:
     """C-ABI kf_set_host_path: KF_HOST_AUTO / KF_HOST_COPY / KF_HOST_DIRECT."""
     _check(load().kf_set_host_path(int(mode)))
+
+
+def kf_set_device_wait_limit(polls: int) -> None:
+    """C-ABI kf_set_device_wait_limit: polls before a staged kernel's compute
+    warps give up a tile wait (0 .. 2^24; -1 = the default)."""
+    _check(load().kf_set_device_wait_limit(int(polls)))
 
 
 def kf_take_device_error() -> int:

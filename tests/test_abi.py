@@ -22,7 +22,7 @@ def test_exports_every_declared_function(lib):
 
 
 def test_version(lib):
-    assert kf.kf_version() == 301  # KF_VERSION of include/kf.h
+    assert kf.kf_version() == 400  # KF_VERSION of include/kf.h
 
 
 def _call(lib, name, params, layout):
@@ -104,3 +104,14 @@ def test_host_entry_argument_checks_without_gpu(lib):
                                               kf.make_layout(0, 0, 10), *[None] * 8, 0, None,
                                               0, None)
     assert rc == kf.KF_ERR_ARG
+
+
+def test_device_wait_limit_range(lib):
+    # host-side argument check only (no CUDA call)
+    for bad in (-2, (1 << 24) + 1, 1 << 40):
+        with pytest.raises(kf.KfError) as e:
+            kf.kf_set_device_wait_limit(bad)
+        assert e.value.code == kf.KF_ERR_ARG
+    kf.kf_set_device_wait_limit(1 << 24)
+    kf.kf_set_device_wait_limit(0)
+    kf.kf_set_device_wait_limit(-1)

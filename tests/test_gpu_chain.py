@@ -174,8 +174,7 @@ def test_chain_matches_oracle_on_256_events(dev, chain_full, chain_sample, preci
     o_st, o_cv, o_stat = oracle_chain(cw, idx, VARIANT_FORM[precision])
     rep = compare.compare(st.T[idx], cv.T[idx], stat[idx], o_st, o_cv, o_stat,
                           on_cylinder=ends_on_cylinder(cw, o_st))
-    parity_log.record("chain", rep)
-    assert rep["ok"], rep
+    parity_log.expect_ok("chain", rep)
 
 
 def test_empty_chain_and_bad_layers(dev):
@@ -216,8 +215,7 @@ def test_adaptive_chain_redo_pass(dev, chain_full):
     o_st, o_cv, o_stat = oracle_chain(cw, idx, oracle.FORM_STANDARD)
     rep = compare.compare(ada[0].T[idx], ada[1].T[idx], ada[2][idx], o_st, o_cv, o_stat,
                           on_cylinder=ends_on_cylinder(cw, o_st))
-    parity_log.record("chain", rep)
-    assert rep["ok"], {k: rep.get(k) for k in ("param", "cov", "worst_param", "worst_cov")}
+    parity_log.expect_ok("chain", rep)
     # the status array is required
     with pytest.raises(kf.KfError) as e:
         kf.kf_kalman_chain(kf.make_params(cw.bz, kf.KF_ADAPTIVE), dc.layout, dc.state, dc.cov,

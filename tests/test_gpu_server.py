@@ -203,8 +203,7 @@ def test_server_results_match_the_oracle(dev, events, precision, host_path):
                 on_cyl |= np.abs(r - R) <= 1e-5 * R
             rep = compare.compare(outs[0].numpy().T, outs[1].numpy().T, outs[2].numpy(), o_st,
                                   o_cv, o_stat, on_cylinder=on_cyl & ~on_plane)
-            parity_log.record("server", rep)
-            assert rep["ok"], rep
+            parity_log.expect_ok("server", rep)
     finally:
         srv.close()
 
