@@ -116,11 +116,21 @@ typedef struct {
                                points and the server use their own (the
                                host-array direct path: the workspace, or
                                the no-allocation call's staging buffer).    */
+#define KF_DF_UPDATE      5 /* FP32 propagation; S^-1, K and C'' in
+                               double-float: each quantity an unevaluated sum
+                               of two floats (about 48 significant bits) with
+                               error-free sums and products (Knuth's two-sum,
+                               the FMA two-product, the double-word add and
+                               multiply of Joldes, Muller and Popescu 2017).
+                               Same algebra as KF_FP64_UPDATE at FP32
+                               instruction rates (GB300 issues FP64 at 1/64 of
+                               FP32).  In the chain the state is rounded to
+                               FP32 between layers, as for KF_FP64_UPDATE.   */
 
 typedef struct {
     float    bz;        /* field along +z in tesla                          */
-    int32_t  precision; /* KF_FP32, KF_FP64_UPDATE, KF_JOSEPH, KF_FP64 or
-                           KF_ADAPTIVE                                      */
+    int32_t  precision; /* KF_FP32, KF_FP64_UPDATE, KF_JOSEPH, KF_FP64,
+                           KF_ADAPTIVE or KF_DF_UPDATE                      */
     uint32_t flags;     /* reserved, must be 0                              */
 } kf_params;
 

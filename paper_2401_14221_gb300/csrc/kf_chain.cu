@@ -127,7 +127,7 @@ extern "C" int kf_kalman_chain(const kf_params *params, kf_layout layout, float 
   clear_error();
   if (!params) return set_error(KF_ERR_ARG, "params is NULL");
   if (params->flags != 0) return set_error(KF_ERR_ARG, "params->flags must be 0");
-  if (params->precision < KF_FP32 || params->precision > KF_ADAPTIVE)
+  if (params->precision < KF_FP32 || params->precision > KF_DF_UPDATE)
     return set_error(KF_ERR_ARG, "unknown precision %d", params->precision);
   LayoutDesc d;
   if (int rc = check_layout(layout, &d)) return rc;
@@ -185,6 +185,7 @@ extern "C" int kf_kalman_chain(const kf_params *params, kf_layout layout, float 
     case KF_FP64_UPDATE: chain_kernel<kFP64Update><<<(unsigned)blocks, threads, 0, s>>>(a); break;
     case KF_JOSEPH: chain_kernel<kJoseph><<<(unsigned)blocks, threads, 0, s>>>(a); break;
     case KF_FP64: chain_kernel<kFP64><<<(unsigned)blocks, threads, 0, s>>>(a); break;
+    case KF_DF_UPDATE: chain_kernel<kDFUpdate><<<(unsigned)blocks, threads, 0, s>>>(a); break;
     default: chain_mark_kernel<<<(unsigned)blocks, threads, 0, s>>>(a); break;
   }
   if (int rc = check_cuda(cudaGetLastError(), "chain launch")) return rc;

@@ -47,6 +47,20 @@ struct HitCursor {
 #pragma unroll
     for (int c = 0; c < 6; ++c) h.hc[c] = __ldg(cp + c * s6);
   }
+  // What a layer of the given kind measures: a plane only x, y and their
+  // 2x2 covariance (the rest is set to 0 and not read).
+  __device__ __forceinline__ void load(LayerHit &h, int kind) const {
+    if (kind != kP2z) {
+      load(h);
+      return;
+    }
+    h.hx = __ldg(hp);
+    h.hy = __ldg(hp + s3);
+    h.hz = 0.0f;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) h.hc[c] = __ldg(cp + c * s6);
+    h.hc[3] = h.hc[4] = h.hc[5] = 0.0f;
+  }
   __device__ __forceinline__ void next_layer() {
     hp += hit_stride;
     cp += hc_stride;
@@ -54,7 +68,7 @@ struct HitCursor {
 };
 
 // Run one track (p, C in registers) through layers 0..L-1 in float
-// arithmetic (kFP32, kJoseph, kFP64Update); the next layer's hit is loaded
+// arithmetic (kFP32, kJoseph, kFP64Update, kDFUpdate); the next layer's hit is loaded
 // while the current layer computes.  Returns the OR of the per-layer status
 // bits.
 template <int VARIANT>
@@ -63,17 +77,18 @@ __device__ __forceinline__ unsigned chain_track(float (&p)[6], float (&C)[21], f
                                                 const float *hits, int64_t hit_stride,
                                                 const float *hitcovs, int64_t hc_stride,
                                                 const ChainLoc &l3, const ChainLoc &l6) {
-  static_assert(VARIANT == kFP32 || VARIANT == kJoseph || VARIANT == kFP64Update,
+  static_assert(VARIANT == kFP32 || VARIANT == kJoseph || VARIANT == kFP64Update ||
+                    VARIANT == kDFUpdate,
                 "float-state chain variants only");
   unsigned st = 0;
   HitCursor cur(hits, hit_stride, hitcovs, hc_stride, l3, l6);
   LayerHit next;
-  cur.load(next);
+  cur.load(next, kinds[0]);
   for (int l = 0; l < L; ++l) {
     const LayerHit h = next;
     if (l + 1 < L) {
       cur.next_layer();
-      cur.load(next);
+      cur.load(next, kinds[l + 1]);
     }
     if (kinds[l] == kP2z)
       st |= p2z_step<VARIANT>(p, C, qf, bz, pos[l], h.hx, h.hy, h.hc[0], h.hc[1], h.hc[2]);
@@ -102,8 +117,9 @@ __device__ __forceinline__ unsigned chain_track_fp64(float (&pf)[6], float (&Cf)
   HitCursor cur(hits, hit_stride, hitcovs, hc_stride, l3, l6);
   for (int l = 0; l < L; ++l, cur.next_layer()) {
     LayerHit h;
-    cur.load(h);
-    double hc[6], shrink, rcos;
+    cur.load(h, kinds[l]);
+    double hc[6], rcos;
+    bool shrink;
     for (int c = 0; c < 6; ++c) hc[c] = h.hc[c];
     if (kinds[l] == kP2z)
       st |= p2z_step_t<double, kStandard>(p, C, (double)qf, (double)bz, (double)pos[l],
@@ -134,12 +150,12 @@ __device__ __forceinline__ unsigned chain_track_marking(float (&p)[6], float (&C
   unsigned st = 0;
   HitCursor cur(hits, hit_stride, hitcovs, hc_stride, l3, l6);
   LayerHit next;
-  cur.load(next);
+  cur.load(next, kinds[0]);
   for (int l = 0; l < L; ++l) {
     const LayerHit h = next;
     if (l + 1 < L) {
       cur.next_layer();
-      cur.load(next);
+      cur.load(next, kinds[l + 1]);
     }
     const unsigned sl =
         kinds[l] == kP2z

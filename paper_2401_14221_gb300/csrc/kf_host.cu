@@ -190,7 +190,7 @@ int run_host(int kind, const kf_params *params, kf_layout layout, const float *s
   clear_error();
   if (!params) return set_error(KF_ERR_ARG, "params is NULL");
   if (params->flags != 0) return set_error(KF_ERR_ARG, "params->flags must be 0");
-  if (params->precision < KF_FP32 || params->precision > KF_ADAPTIVE)
+  if (params->precision < KF_FP32 || params->precision > KF_DF_UPDATE)
     return set_error(KF_ERR_ARG, "unknown precision %d", params->precision);
   LayoutDesc d;
   if (int rc = check_layout(layout, &d)) return rc;

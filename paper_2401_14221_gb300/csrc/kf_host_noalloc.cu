@@ -124,7 +124,7 @@ extern "C" int kf_propagate_update_host_noalloc(int32_t kind, const kf_params *p
     return set_error(KF_ERR_ARG, "kind = %d is neither KF_P2Z nor KF_P2R", kind);
   if (!params) return set_error(KF_ERR_ARG, "params is NULL");
   if (params->flags != 0) return set_error(KF_ERR_ARG, "params->flags must be 0");
-  if (params->precision < KF_FP32 || params->precision > KF_ADAPTIVE)
+  if (params->precision < KF_FP32 || params->precision > KF_DF_UPDATE)
     return set_error(KF_ERR_ARG, "unknown precision %d", params->precision);
   LayoutDesc d;
   if (int rc = check_layout(layout, &d)) return rc;

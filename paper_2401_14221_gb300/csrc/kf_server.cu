@@ -394,6 +394,7 @@ bool launch_batch(kf_server *s, std::vector<Request *> &batch) {
       case KF_FP64_UPDATE: batch_chain_kernel<kFP64Update><<<g, 256, 0, s->s_compute>>>(a); break;
       case KF_JOSEPH: batch_chain_kernel<kJoseph><<<g, 256, 0, s->s_compute>>>(a); break;
       case KF_FP64: batch_chain_kernel<kFP64><<<g, 256, 0, s->s_compute>>>(a); break;
+      case KF_DF_UPDATE: batch_chain_kernel<kDFUpdate><<<g, 256, 0, s->s_compute>>>(a); break;
       default:
         batch_chain_kernel<kAdaptive><<<g, 256, 0, s->s_compute>>>(a);
         e = cudaGetLastError();
@@ -571,7 +572,7 @@ extern "C" int kf_server_create(const kf_server_config *cfg, kf_server **out) {
   for (int l = 0; l < cfg->L; ++l)
     if (cfg->layers[l].kind != KF_P2Z && cfg->layers[l].kind != KF_P2R)
       return set_error(KF_ERR_ARG, "layers[%d].kind = %d", l, cfg->layers[l].kind);
-  if (cfg->precision < KF_FP32 || cfg->precision > KF_ADAPTIVE)
+  if (cfg->precision < KF_FP32 || cfg->precision > KF_DF_UPDATE)
     return set_error(KF_ERR_ARG, "unknown precision %d", cfg->precision);
   if (cfg->max_events_in_flight < 1)
     return set_error(KF_ERR_ARG, "max_events_in_flight must be >= 1");

@@ -170,7 +170,7 @@ static int launch_step(const kf_params *params, kf_layout layout, const float *s
   clear_error();
   if (!params) return set_error(KF_ERR_ARG, "params is NULL");
   if (params->flags != 0) return set_error(KF_ERR_ARG, "params->flags must be 0");
-  if (params->precision < KF_FP32 || params->precision > KF_ADAPTIVE)
+  if (params->precision < KF_FP32 || params->precision > KF_DF_UPDATE)
     return set_error(KF_ERR_ARG, "unknown precision %d", params->precision);
   LayoutDesc d;
   if (int rc = check_layout(layout, &d)) return rc;
@@ -270,6 +270,7 @@ static int launch_step_main(int kind, int precision, const StepArgs &a, cudaStre
         case KF_FP64_UPDATE: step_kernel_strided<kP2z, kFP64Update><<<g, 256, 0, s>>>(a); break;
         case KF_JOSEPH: step_kernel_strided<kP2z, kJoseph><<<g, 256, 0, s>>>(a); break;
         case KF_FP64: step_kernel_strided<kP2z, kFP64><<<g, 256, 0, s>>>(a); break;
+        case KF_DF_UPDATE: step_kernel_strided<kP2z, kDFUpdate><<<g, 256, 0, s>>>(a); break;
         default: step_kernel_strided<kP2z, kAdaptive><<<g, 256, 0, s>>>(a); break;
       }
     } else {
@@ -278,6 +279,7 @@ static int launch_step_main(int kind, int precision, const StepArgs &a, cudaStre
         case KF_FP64_UPDATE: step_kernel_strided<kP2r, kFP64Update><<<g, 256, 0, s>>>(a); break;
         case KF_JOSEPH: step_kernel_strided<kP2r, kJoseph><<<g, 256, 0, s>>>(a); break;
         case KF_FP64: step_kernel_strided<kP2r, kFP64><<<g, 256, 0, s>>>(a); break;
+        case KF_DF_UPDATE: step_kernel_strided<kP2r, kDFUpdate><<<g, 256, 0, s>>>(a); break;
         default: step_kernel_strided<kP2r, kAdaptive><<<g, 256, 0, s>>>(a); break;
       }
     }
@@ -302,6 +304,7 @@ static int launch_step_main(int kind, int precision, const StepArgs &a, cudaStre
       case KF_FP64_UPDATE: e = cudaLaunchKernelEx(&lc, step_kernel<kP2z, kFP64Update>, a); break;
       case KF_JOSEPH: e = cudaLaunchKernelEx(&lc, step_kernel<kP2z, kJoseph>, a); break;
       case KF_FP64: e = cudaLaunchKernelEx(&lc, step_kernel<kP2z, kFP64>, a); break;
+      case KF_DF_UPDATE: e = cudaLaunchKernelEx(&lc, step_kernel<kP2z, kDFUpdate>, a); break;
       default: e = cudaLaunchKernelEx(&lc, step_kernel<kP2z, kAdaptive>, a); break;
     }
   } else {
@@ -310,6 +313,7 @@ static int launch_step_main(int kind, int precision, const StepArgs &a, cudaStre
       case KF_FP64_UPDATE: e = cudaLaunchKernelEx(&lc, step_kernel<kP2r, kFP64Update>, a); break;
       case KF_JOSEPH: e = cudaLaunchKernelEx(&lc, step_kernel<kP2r, kJoseph>, a); break;
       case KF_FP64: e = cudaLaunchKernelEx(&lc, step_kernel<kP2r, kFP64>, a); break;
+      case KF_DF_UPDATE: e = cudaLaunchKernelEx(&lc, step_kernel<kP2r, kDFUpdate>, a); break;
       default: e = cudaLaunchKernelEx(&lc, step_kernel<kP2r, kAdaptive>, a); break;
     }
   }

@@ -50,7 +50,8 @@ __device__ __forceinline__ unsigned redo_track_fp64(const StepArgs &a, int64_t i
     b3 = blk * 3 * W + r;
     s = W;
   }
-  double p[6], C[21], hc[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0}, shrink, cinc;
+  double p[6], C[21], hc[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0}, cinc;
+  bool shrink;
 #pragma unroll
   for (int c = 0; c < 6; ++c) p[c] = a.state_in[b6 + c * s];
 #pragma unroll

@@ -134,7 +134,8 @@ __global__ void __launch_bounds__(256)
     const Loc l6 = locate<6>(i, a.n, a.soa, a.lw);
     const Loc l15 = locate<15>(i, a.n, a.soa, a.lw);
     const Loc l3 = locate<3>(i, a.n, a.soa, a.lw);
-    double p[6], C[21], hc[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0}, shrink, cinc;
+    double p[6], C[21], hc[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0}, cinc;
+    bool shrink;
     load_compressed(a, l6, l15, p, C);
     constexpr int nhc = KIND == kP2z ? 3 : 6;
 #pragma unroll
@@ -174,7 +175,7 @@ extern "C" int kf_propagate_update_compressed(
     return set_error(KF_ERR_ARG, "kind = %d is neither KF_P2Z nor KF_P2R", kind);
   if (!params) return set_error(KF_ERR_ARG, "params is NULL");
   if (params->flags != 0) return set_error(KF_ERR_ARG, "params->flags must be 0");
-  if (params->precision < KF_FP32 || params->precision > KF_ADAPTIVE)
+  if (params->precision < KF_FP32 || params->precision > KF_DF_UPDATE)
     return set_error(KF_ERR_ARG, "unknown precision %d", params->precision);
   LayoutDesc d;
   if (int rc = check_layout(layout, &d)) return rc;
@@ -230,6 +231,7 @@ extern "C" int kf_propagate_update_compressed(
       case KF_FP64_UPDATE: step_compressed_kernel<kP2z, kFP64Update><<<g, threads, 0, s>>>(a); break;
       case KF_JOSEPH: step_compressed_kernel<kP2z, kJoseph><<<g, threads, 0, s>>>(a); break;
       case KF_FP64: step_compressed_kernel<kP2z, kFP64><<<g, threads, 0, s>>>(a); break;
+      case KF_DF_UPDATE: step_compressed_kernel<kP2z, kDFUpdate><<<g, threads, 0, s>>>(a); break;
       default: step_compressed_kernel<kP2z, kAdaptive><<<g, threads, 0, s>>>(a); break;
     }
   } else {
@@ -238,6 +240,7 @@ extern "C" int kf_propagate_update_compressed(
       case KF_FP64_UPDATE: step_compressed_kernel<kP2r, kFP64Update><<<g, threads, 0, s>>>(a); break;
       case KF_JOSEPH: step_compressed_kernel<kP2r, kJoseph><<<g, threads, 0, s>>>(a); break;
       case KF_FP64: step_compressed_kernel<kP2r, kFP64><<<g, threads, 0, s>>>(a); break;
+      case KF_DF_UPDATE: step_compressed_kernel<kP2r, kDFUpdate><<<g, threads, 0, s>>>(a); break;
       default: step_compressed_kernel<kP2r, kAdaptive><<<g, threads, 0, s>>>(a); break;
     }
   }

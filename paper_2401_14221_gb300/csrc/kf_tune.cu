@@ -289,7 +289,7 @@ extern "C" int kf_autotune_import(const char *text) {
                &lw, &nb, &kern, &thr, &cps, &ms) != 10)
       return set_error(KF_ERR_ARG, "line %d: malformed entry", lineno);
     if ((op != kOpStep && op != kOpChain) || (kind != KF_P2Z && kind != KF_P2R) ||
-        prec < KF_FP32 || prec > KF_ADAPTIVE || (soa != 0 && soa != 1) || lw < 0 || lw > 7 ||
+        prec < KF_FP32 || prec > KF_DF_UPDATE || (soa != 0 && soa != 1) || lw < 0 || lw > 7 ||
         (kern != KF_STEP_DIRECT && kern != KF_STEP_STAGED) ||
         (thr != 64 && thr != 128 && thr != 256) || cps < 0 || cps > 3 || !(ms >= 0.0f))
       return set_error(KF_ERR_ARG, "line %d: value out of range", lineno);

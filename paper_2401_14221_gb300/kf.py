@@ -25,7 +25,7 @@ HEADER = os.path.join(os.path.dirname(_PKG), "include", "kf.h")
 KF_OK, KF_ERR_ARG, KF_ERR_CUDA, KF_ERR_UNSUPPORTED, KF_ERR_TIMEOUT = 0, 1, 2, 3, 4
 NO_INTERSECT, S_NOT_PD, BAD_K, NONFINITE = 1, 2, 4, 8
 KF_SOA, KF_AOSOA = 0, 1
-KF_FP32, KF_FP64_UPDATE, KF_JOSEPH, KF_FP64, KF_ADAPTIVE = 0, 1, 2, 3, 4
+KF_FP32, KF_FP64_UPDATE, KF_JOSEPH, KF_FP64, KF_ADAPTIVE, KF_DF_UPDATE = 0, 1, 2, 3, 4, 5
 
 
 class KfError(RuntimeError):

@@ -16,7 +16,8 @@ from paper_2401_14221_gb300 import workload as W
 
 pytestmark = pytest.mark.gpu
 
-VARIANT_FORM = {kf.KF_FP32: oracle.FORM_STANDARD, kf.KF_FP64_UPDATE: oracle.FORM_STANDARD,
+VARIANT_FORM = {kf.KF_DF_UPDATE: oracle.FORM_STANDARD,
+                kf.KF_FP32: oracle.FORM_STANDARD, kf.KF_FP64_UPDATE: oracle.FORM_STANDARD,
                 kf.KF_JOSEPH: oracle.FORM_JOSEPH, kf.KF_FP64: oracle.FORM_STANDARD,
                 kf.KF_ADAPTIVE: oracle.FORM_STANDARD}
 
@@ -92,7 +93,7 @@ def ends_on_cylinder(cw, o_st):
 
 @pytest.mark.parametrize("kind", [W.P2Z, W.P2R])
 @pytest.mark.parametrize("layout", [(kf.KF_SOA, 0), (kf.KF_AOSOA, 32)])
-@pytest.mark.parametrize("precision", [kf.KF_FP32, kf.KF_FP64, kf.KF_ADAPTIVE])
+@pytest.mark.parametrize("precision", [kf.KF_FP32, kf.KF_FP64, kf.KF_ADAPTIVE, kf.KF_DF_UPDATE])
 def test_chain_of_one_layer_equals_single_step_bitwise(dev, kind, layout, precision):
     w = W.make_p2z(20011, seed=41) if kind == W.P2Z else W.make_p2r(1, 20011, seed=41)
     b = kf.upload(w, layout[0], layout[1], dev)
@@ -110,7 +111,7 @@ def test_chain_of_one_layer_equals_single_step_bitwise(dev, kind, layout, precis
         assert np.array_equal(a, c)
 
 
-@pytest.mark.parametrize("precision", [kf.KF_FP32, kf.KF_JOSEPH])
+@pytest.mark.parametrize("precision", [kf.KF_FP32, kf.KF_JOSEPH, kf.KF_DF_UPDATE])
 def test_chain_equals_per_layer_launches_bitwise(dev, precision):
     cw = W.make_chain(events=6, seed=42)
     dc = kf.chain_upload(cw, kf.KF_AOSOA, 32, dev)
@@ -157,7 +158,8 @@ def chain_sample(chain_full):
     return idx, ill_conditioned(chain_full, idx)
 
 
-@pytest.mark.parametrize("precision", [kf.KF_FP32, kf.KF_FP64_UPDATE, kf.KF_JOSEPH, kf.KF_FP64,
+@pytest.mark.parametrize("precision", [kf.KF_FP32, kf.KF_FP64_UPDATE, kf.KF_DF_UPDATE,
+                                       kf.KF_JOSEPH, kf.KF_FP64,
                                        kf.KF_ADAPTIVE])
 def test_chain_matches_oracle_on_256_events(dev, chain_full, chain_sample, precision):
     cw = chain_full
@@ -165,7 +167,7 @@ def test_chain_matches_oracle_on_256_events(dev, chain_full, chain_sample, preci
     dc.run(precision)
     st, cv, stat = dc.download()
     idx, ill = chain_sample
-    if precision in (kf.KF_FP32, kf.KF_FP64_UPDATE, kf.KF_JOSEPH):
+    if precision in (kf.KF_FP32, kf.KF_FP64_UPDATE, kf.KF_DF_UPDATE, kf.KF_JOSEPH):
         # float-state variants meet the bounds on well-conditioned tracks
         # only (about 0.1 % of this workload crosses a layer at grazing
         # incidence; KF_ADAPTIVE and KF_FP64 are checked on every track)

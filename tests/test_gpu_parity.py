@@ -25,8 +25,9 @@ LAYOUTS = [(kf.KF_SOA, 0), (kf.KF_AOSOA, 16), (kf.KF_AOSOA, 32), (kf.KF_AOSOA, 6
            (kf.KF_AOSOA, 128)]
 VARIANT_FORM = {kf.KF_FP32: oracle.FORM_STANDARD, kf.KF_FP64_UPDATE: oracle.FORM_STANDARD,
                 kf.KF_JOSEPH: oracle.FORM_JOSEPH, kf.KF_FP64: oracle.FORM_STANDARD,
-                kf.KF_ADAPTIVE: oracle.FORM_STANDARD}
-ALL_VARIANTS = [kf.KF_FP32, kf.KF_FP64_UPDATE, kf.KF_JOSEPH, kf.KF_FP64, kf.KF_ADAPTIVE]
+                kf.KF_ADAPTIVE: oracle.FORM_STANDARD, kf.KF_DF_UPDATE: oracle.FORM_STANDARD}
+ALL_VARIANTS = [kf.KF_FP32, kf.KF_FP64_UPDATE, kf.KF_JOSEPH, kf.KF_FP64, kf.KF_ADAPTIVE,
+                kf.KF_DF_UPDATE]
 
 
 @pytest.fixture(scope="module")
@@ -153,7 +154,7 @@ def test_precision_study_pt_0p2_to_100(dev, w_prec, precision, step_kernel):
 
 
 @pytest.mark.parametrize("layout", LAYOUTS[1:])
-@pytest.mark.parametrize("precision", [kf.KF_FP32, kf.KF_JOSEPH, kf.KF_ADAPTIVE])
+@pytest.mark.parametrize("precision", ALL_VARIANTS)
 def test_staged_and_direct_kernels_agree_bitwise(dev, w_p2r, layout, precision):
     # the kernels run the same per-track arithmetic; only the loads differ
     # (staged: 2 CTAs/SM x 3 stages and 3 CTAs/SM x 2 stages, the latter
