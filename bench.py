@@ -526,9 +526,12 @@ def serving_bench(args, kf, W, dev, rank):
         return arrivals, {"rate_events_per_s": rate, "tracks_per_s": tracks / (t_end - t0),
                           "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"], "max_ms": st["max_ms"],
                           "batches": st["batches"], "max_batch_events": st["max_batch_events"],
+                          "scheduler_ms": {"longest_pass": st["sched_pass_max_ms"],
+                                           "longest_gap_while_busy": st["sched_gap_max_ms"]},
                           "phases_ms": {ph: [st[f"{ph}_p50_ms"], st[f"{ph}_p99_ms"]]
                                         for ph in ("queue", "ready", "copyin", "compute",
-                                                   "out")}}
+                                                   "out", "gpu_copyin", "gpu_compute",
+                                                   "gpu_out", "copyin_issue")}}
 
     runs = [serve(rate, 12 + rank + k) for k, rate in enumerate(args.serve_rates)]
     runs_copy = [serve(rate, 12 + rank + k, kf.KF_HOST_COPY)[1]

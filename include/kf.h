@@ -499,6 +499,20 @@ typedef struct {
     /* the copy-in part of 'ready': admitted -> its copies seen landed (the
      * rest of 'ready' is waiting for the batch in flight to finish) */
     double  copyin_p50_ms, copyin_p99_ms;
+    /* The device's own durations, from timing events recorded in the
+     * streams around the work (0 where an event has no such work: a direct
+     * event copies nothing): its copies in, its batch's kernel(s), its copies
+     * out.  The host-observed phase minus the device duration is time the
+     * work waited in its stream or the scheduler took to notice it. */
+    double  gpu_copyin_p50_ms, gpu_copyin_p99_ms;
+    double  gpu_compute_p50_ms, gpu_compute_p99_ms;
+    double  gpu_out_p50_ms, gpu_out_p99_ms;
+    /* host time the scheduler spent in the calls that enqueue the copies in
+     * (part of copyin; 0 for a direct event) */
+    double  copyin_issue_p50_ms, copyin_issue_p99_ms;
+    /* the scheduler thread's longest pass, and its longest absence between
+     * passes while GPU work was in flight (ms) */
+    double  sched_pass_max_ms, sched_gap_max_ms;
 } kf_server_stats;
 
 /* Arena bytes one copied event of n tracks and L layers occupies (-1 if

@@ -225,7 +225,12 @@ struct Request {
   int64_t off = -1;  // arena offset
   Layout lay{};
   cudaEvent_t ev = nullptr;  // copies in / copies out landed
-  std::chrono::steady_clock::time_point t_submit, t_admit, t_copied, t_launch, t_finished, t_done;
+  // timing events around the copies in (then around the copies out) on the
+  // GPU, for the device-side durations of the phases
+  cudaEvent_t g0 = nullptr, g1 = nullptr;
+  std::chrono::steady_clock::time_point t_submit, t_admit, t_issued, t_copied, t_launch,
+      t_finished, t_done;
+  float gpu_in_ms = 0.0f, gpu_compute_ms = 0.0f, gpu_out_ms = 0.0f;
   bool copied = false;  // copy-in seen complete (t_copied set)
 };
 
@@ -286,7 +291,13 @@ struct kf_server {
   int in_flight = 0;  // admitted, not yet done
   // statistics
   std::vector<double> latencies_ms;
-  std::vector<double> phase_ms[5];  // queue, ready, compute, out, copy-in
+  // queue, ready, compute, out, copy-in (as the scheduler observes them),
+  // then the device-side durations of the copies in, the batch kernel(s)
+  // and the copies out, then the host time spent issuing the copies in
+  std::vector<double> phase_ms[9];
+  double sched_pass_max_ms = 0.0, sched_gap_max_ms = 0.0;
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> timing_pool;
+  cudaEvent_t batch_g0 = nullptr, batch_g1 = nullptr;
   int64_t tracks_done = 0, batches = 0, max_batch_events = 0;
 };
 
@@ -306,7 +317,9 @@ void fail_locked(kf_server *s, cudaError_t e, const char *what) {
 bool start_copy_in(kf_server *s, Request *r) {
   char *b = s->arena_base + r->off;
   const int64_t n = r->n, L = s->cfg.L;
-  cudaError_t e = cudaMemcpyAsync(b + r->lay.state, r->state, 4 * 6 * n, cudaMemcpyDefault, s->s_in);
+  cudaError_t e = cudaEventRecord(r->g0, s->s_in);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(b + r->lay.state, r->state, 4 * 6 * n, cudaMemcpyDefault, s->s_in);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(b + r->lay.cov, r->cov, 4 * 21 * n, cudaMemcpyDefault, s->s_in);
   if (e == cudaSuccess)
@@ -315,6 +328,7 @@ bool start_copy_in(kf_server *s, Request *r) {
     e = cudaMemcpyAsync(b + r->lay.hits, r->hits, 4 * 3 * n * L, cudaMemcpyDefault, s->s_in);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(b + r->lay.hitcovs, r->hitcovs, 4 * 6 * n * L, cudaMemcpyDefault, s->s_in);
+  if (e == cudaSuccess) e = cudaEventRecord(r->g1, s->s_in);
   if (e == cudaSuccess) e = cudaEventRecord(r->ev, s->s_in);
   if (e != cudaSuccess) {
     fail_locked(s, e, "server copy in");
@@ -327,12 +341,14 @@ bool start_copy_out(kf_server *s, Request *r) {
   char *b = s->arena_base + r->off;
   const int64_t n = r->n;
   cudaError_t e = cudaStreamWaitEvent(s->s_out, s->batch_ev, 0);
+  if (e == cudaSuccess) e = cudaEventRecord(r->g0, s->s_out);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(r->state_out, b + r->lay.state, 4 * 6 * n, cudaMemcpyDefault, s->s_out);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(r->cov_out, b + r->lay.cov, 4 * 21 * n, cudaMemcpyDefault, s->s_out);
   if (e == cudaSuccess && r->status_out)
     e = cudaMemcpyAsync(r->status_out, b + r->lay.status, n, cudaMemcpyDefault, s->s_out);
+  if (e == cudaSuccess) e = cudaEventRecord(r->g1, s->s_out);
   if (e == cudaSuccess) e = cudaEventRecord(r->ev, s->s_out);
   if (e != cudaSuccess) {
     fail_locked(s, e, "server copy out");
@@ -387,6 +403,7 @@ bool launch_batch(kf_server *s, std::vector<Request *> &batch) {
     e = cudaStreamWaitEvent(s->s_compute, r->ev, 0);
     if (e != cudaSuccess) break;
   }
+  if (e == cudaSuccess) e = cudaEventRecord(s->batch_g0, s->s_compute);
   if (e == cudaSuccess && blocks > 0) {
     const unsigned g = (unsigned)blocks;
     switch (s->cfg.precision) {
@@ -405,6 +422,7 @@ bool launch_batch(kf_server *s, std::vector<Request *> &batch) {
     }
     if (e == cudaSuccess) e = cudaGetLastError();
   }
+  if (e == cudaSuccess) e = cudaEventRecord(s->batch_g1, s->s_compute);
   if (e == cudaSuccess) e = cudaEventRecord(s->batch_ev, s->s_compute);
   if (e != cudaSuccess) {
     fail_locked(s, e, "server batch launch");
@@ -429,10 +447,15 @@ void finish_request(kf_server *s, Request *r) {
   s->phase_ms[2].push_back(ms(r->t_launch, r->t_finished));
   s->phase_ms[3].push_back(ms(r->t_finished, r->t_done));
   s->phase_ms[4].push_back(ms(r->t_admit, r->t_copied));
+  s->phase_ms[5].push_back(r->gpu_in_ms);
+  s->phase_ms[6].push_back(r->gpu_compute_ms);
+  s->phase_ms[7].push_back(r->gpu_out_ms);
+  s->phase_ms[8].push_back(ms(r->t_admit, r->t_issued));
   s->tracks_done += r->n;
   s->arena.release(r->off, r->lay.bytes);
   s->event_pool.push_back(r->ev);
-  r->ev = nullptr;
+  s->timing_pool.emplace_back(r->g0, r->g1);
+  r->ev = r->g0 = r->g1 = nullptr;
   s->in_flight -= 1;
   s->cv_done.notify_all();
 }
@@ -449,6 +472,7 @@ bool schedule_once(kf_server *s) {
       continue;
     }
     if (q != cudaSuccess) fail_locked(s, q, "server copy-out completion");
+    if (q == cudaSuccess) cudaEventElapsedTime(&r->gpu_out_ms, r->g0, r->g1);
     finish_request(s, r);
     s->returning.erase(s->returning.begin() + k);
     moved = true;
@@ -460,8 +484,11 @@ bool schedule_once(kf_server *s) {
     if (q != cudaErrorNotReady) {
       if (q != cudaSuccess) fail_locked(s, q, "server batch completion");
       const auto now = std::chrono::steady_clock::now();
+      float gpu_ms = 0.0f;
+      if (q == cudaSuccess) cudaEventElapsedTime(&gpu_ms, s->batch_g0, s->batch_g1);
       for (Request *r : s->running) {
         r->t_finished = now;
+        r->gpu_compute_ms = gpu_ms;
         if (r->direct) {
           finish_request(s, r);
         } else if (start_copy_out(s, r)) {
@@ -477,7 +504,7 @@ bool schedule_once(kf_server *s) {
   if (s->paused || s->error != KF_OK) return moved;
   // admit while a slot, an event object and arena space are free
   while (!s->pending.empty() && s->in_flight < s->cfg.max_events_in_flight &&
-         !s->event_pool.empty()) {
+         !s->event_pool.empty() && !s->timing_pool.empty()) {
     Request *r = s->pending.front();
     const int64_t off = s->arena.alloc(r->lay.bytes);
     if (off < 0) break;  // wait for space: first come, first served
@@ -485,13 +512,18 @@ bool schedule_once(kf_server *s) {
     r->t_admit = std::chrono::steady_clock::now();
     r->ev = s->event_pool.back();
     s->event_pool.pop_back();
+    r->g0 = s->timing_pool.back().first;
+    r->g1 = s->timing_pool.back().second;
+    s->timing_pool.pop_back();
     s->pending.pop_front();
     s->in_flight += 1;
     if (r->direct) {  // nothing to copy: ready for the next batch
       r->copied = true;
-      r->t_copied = r->t_admit;
+      r->t_issued = r->t_copied = r->t_admit;
     } else if (!start_copy_in(s, r)) {
       break;
+    } else {
+      r->t_issued = std::chrono::steady_clock::now();
     }
     r->phase = Phase::kCopying;
     s->copying.push_back(r);
@@ -504,6 +536,7 @@ bool schedule_once(kf_server *s) {
       if (!r->copied && cudaEventQuery(r->ev) == cudaSuccess) {
         r->copied = true;
         r->t_copied = now;
+        cudaEventElapsedTime(&r->gpu_in_ms, r->g0, r->g1);
       }
     }
   }
@@ -536,8 +569,20 @@ bool schedule_once(kf_server *s) {
 void scheduler_main(kf_server *s) {
   cudaSetDevice(s->cfg.device);
   std::unique_lock<std::mutex> lock(s->mu);
+  auto last = std::chrono::steady_clock::now();
   while (!s->stop) {
+    // the scheduler's own timing: how long a pass takes, and how long it
+    // was away between passes while GPU work was in flight (the mutex, the
+    // back-off sleep and the OS's scheduling of this thread)
+    const auto t0 = std::chrono::steady_clock::now();
+    const bool was_busy = s->batch_in_flight || !s->copying.empty() || !s->returning.empty();
+    if (was_busy)
+      s->sched_gap_max_ms =
+          std::max(s->sched_gap_max_ms, std::chrono::duration<double, std::milli>(t0 - last).count());
     const bool moved = schedule_once(s);
+    last = std::chrono::steady_clock::now();
+    s->sched_pass_max_ms =
+        std::max(s->sched_pass_max_ms, std::chrono::duration<double, std::milli>(last - t0).count());
     const bool busy = s->batch_in_flight || !s->copying.empty() || !s->returning.empty();
     if (moved) continue;
     if (busy) {
@@ -589,10 +634,19 @@ extern "C" int kf_server_create(const kf_server_config *cfg, kf_server **out) {
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->s_compute, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->s_out, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->batch_ev, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreate(&s->batch_g0);
+  if (e == cudaSuccess) e = cudaEventCreate(&s->batch_g1);
   for (int k = 0; e == cudaSuccess && k < cfg->max_events_in_flight; ++k) {
-    cudaEvent_t ev;
+    cudaEvent_t ev, g0 = nullptr, g1 = nullptr;
     e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
     if (e == cudaSuccess) s->event_pool.push_back(ev);
+    if (e == cudaSuccess) e = cudaEventCreate(&g0);
+    if (e == cudaSuccess) e = cudaEventCreate(&g1);
+    if (e == cudaSuccess) s->timing_pool.emplace_back(g0, g1);
+    else {
+      if (g0) cudaEventDestroy(g0);
+      if (g1) cudaEventDestroy(g1);
+    }
   }
   if (e != cudaSuccess) {
     kf_server_destroy(s);
@@ -745,12 +799,18 @@ extern "C" int kf_server_get_stats(kf_server *s, kf_server_stats *out) {
     for (double x : v) sum += x;
     out->mean_ms = sum / (double)v.size();
   }
-  double *dst[5][2] = {{&out->queue_p50_ms, &out->queue_p99_ms},
+  double *dst[9][2] = {{&out->queue_p50_ms, &out->queue_p99_ms},
                        {&out->ready_p50_ms, &out->ready_p99_ms},
                        {&out->compute_p50_ms, &out->compute_p99_ms},
                        {&out->out_p50_ms, &out->out_p99_ms},
-                       {&out->copyin_p50_ms, &out->copyin_p99_ms}};
-  for (int k = 0; k < 5; ++k) {
+                       {&out->copyin_p50_ms, &out->copyin_p99_ms},
+                       {&out->gpu_copyin_p50_ms, &out->gpu_copyin_p99_ms},
+                       {&out->gpu_compute_p50_ms, &out->gpu_compute_p99_ms},
+                       {&out->gpu_out_p50_ms, &out->gpu_out_p99_ms},
+                       {&out->copyin_issue_p50_ms, &out->copyin_issue_p99_ms}};
+  out->sched_pass_max_ms = s->sched_pass_max_ms;
+  out->sched_gap_max_ms = s->sched_gap_max_ms;
+  for (int k = 0; k < 9; ++k) {
     std::vector<double> w = s->phase_ms[k];
     if (w.empty()) continue;
     std::sort(w.begin(), w.end());
@@ -767,6 +827,7 @@ extern "C" int kf_server_reset_stats(kf_server *s) {
   std::lock_guard<std::mutex> lock(s->mu);
   s->latencies_ms.clear();
   for (auto &w : s->phase_ms) w.clear();
+  s->sched_pass_max_ms = s->sched_gap_max_ms = 0.0;
   s->tracks_done = s->batches = s->max_batch_events = 0;
   return KF_OK;
 }
@@ -805,6 +866,12 @@ extern "C" int kf_server_destroy(kf_server *s) {
     delete kv.second;
   }
   for (cudaEvent_t ev : s->event_pool) cudaEventDestroy(ev);
+  for (auto &g : s->timing_pool) {
+    cudaEventDestroy(g.first);
+    cudaEventDestroy(g.second);
+  }
+  if (s->batch_g0) cudaEventDestroy(s->batch_g0);
+  if (s->batch_g1) cudaEventDestroy(s->batch_g1);
   if (s->batch_ev) cudaEventDestroy(s->batch_ev);
   if (s->s_in) cudaStreamDestroy(s->s_in);
   if (s->s_compute) cudaStreamDestroy(s->s_compute);

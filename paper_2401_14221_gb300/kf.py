@@ -70,7 +70,12 @@ class kf_server_stats(ctypes.Structure):
                 ("ready_p50_ms", ctypes.c_double), ("ready_p99_ms", ctypes.c_double),
                 ("compute_p50_ms", ctypes.c_double), ("compute_p99_ms", ctypes.c_double),
                 ("out_p50_ms", ctypes.c_double), ("out_p99_ms", ctypes.c_double),
-                ("copyin_p50_ms", ctypes.c_double), ("copyin_p99_ms", ctypes.c_double)]
+                ("copyin_p50_ms", ctypes.c_double), ("copyin_p99_ms", ctypes.c_double),
+                ("gpu_copyin_p50_ms", ctypes.c_double), ("gpu_copyin_p99_ms", ctypes.c_double),
+                ("gpu_compute_p50_ms", ctypes.c_double), ("gpu_compute_p99_ms", ctypes.c_double),
+                ("gpu_out_p50_ms", ctypes.c_double), ("gpu_out_p99_ms", ctypes.c_double),
+                ("copyin_issue_p50_ms", ctypes.c_double), ("copyin_issue_p99_ms", ctypes.c_double),
+                ("sched_pass_max_ms", ctypes.c_double), ("sched_gap_max_ms", ctypes.c_double)]
 
 
 _lib = None

@@ -153,6 +153,27 @@ def test_precision_study_pt_0p2_to_100(dev, w_prec, precision, step_kernel):
         check(w, b, sample_indices(w.n), VARIANT_FORM[precision])
 
 
+def test_double_float_update_carries_fp64_update_precision(dev, w_prec):
+    # KF_DF_UPDATE and KF_FP64_UPDATE share the FP32 propagation and compute
+    # S^-1, K and C'' far beyond FP32 (double-float about 48 bits, double 53)
+    # before one rounding to FP32: their results must agree to a few FP32
+    # ulps, much closer than the FP32 update comes to either.  A double-float
+    # step that silently lost its low word would fail the first bound.
+    for w in w_prec:
+        outs = {p: run(w, dev, (kf.KF_AOSOA, 32), p).download()
+                for p in (kf.KF_FP64_UPDATE, kf.KF_DF_UPDATE, kf.KF_FP32)}
+        ref = outs[kf.KF_FP64_UPDATE]
+        on_cyl = cylinder_frame(w, ref[2])
+
+        def rep(o):
+            return compare.compare(o[0].T, o[1].T, o[2], ref[0].T, ref[1].T, ref[2],
+                                   on_cylinder=on_cyl)
+        r_df, r_32 = rep(outs[kf.KF_DF_UPDATE]), rep(outs[kf.KF_FP32])
+        assert r_df["status_equal"]
+        assert r_df["param"]["max"] <= 5e-7 and r_df["cov"]["max"] <= 5e-7, r_df
+        assert r_32["cov"]["max"] > 10 * r_df["cov"]["max"], (r_32["cov"], r_df["cov"])
+
+
 @pytest.mark.parametrize("layout", LAYOUTS[1:])
 @pytest.mark.parametrize("precision", ALL_VARIANTS)
 def test_staged_and_direct_kernels_agree_bitwise(dev, w_p2r, layout, precision):

@@ -155,6 +155,9 @@ def test_direct_events_in_pageable_memory(dev, events):
                 assert np.array_equal(a.numpy(), b)
         st = srv.stats()
         assert st["copyin_p99_ms"] == 0.0 and st["out_p99_ms"] < 1.0
+        # direct events copy nothing: no device copy time either
+        assert st["gpu_copyin_p99_ms"] == 0.0 and st["gpu_out_p99_ms"] == 0.0
+        assert st["gpu_compute_p50_ms"] > 0.0
     finally:
         kf.kf_set_host_path(kf.KF_HOST_AUTO)
         srv.close()
@@ -253,6 +256,14 @@ def test_paused_server_wait_times_out_then_completes(dev, events, host_path):
         assert st["copyin_p50_ms"] <= st["ready_p50_ms"]  # copy-in is part of ready
         assert st["queue_p50_ms"] + st["ready_p50_ms"] + st["compute_p50_ms"] + \
             st["out_p50_ms"] <= st["max_ms"] + 1e-6
+        # the device's own durations (timing events in the streams) fit
+        # inside what the scheduler observed for the phase; a direct event
+        # copies nothing
+        copied = host_path == kf.KF_HOST_COPY
+        for ph in ("copyin", "compute", "out"):
+            assert 0.0 <= st[f"gpu_{ph}_p50_ms"] <= st[f"{ph}_p50_ms"] + 0.05
+            assert st[f"gpu_{ph}_p50_ms"] > 0.0 or (ph != "compute" and not copied)
+        assert st["copyin_issue_p50_ms"] <= st["copyin_p50_ms"]
     finally:
         srv.close()
 
