@@ -47,7 +47,8 @@ BYTES_PER_TRACK_P2Z = 237
 # on 64 events (bench.py --profile-only --kind chain, captured with ncu --set full)
 FLOPS_PER_TRACK_LAYER = 465
 # FP32 peak from the unit counts: 152 SMs x 128 FP32 lanes x 2 flops x clock
-FP32_LANES = 152 * 128
+SMS = 152
+FP32_LANES = SMS * 128
 FALLBACK_HBM_GBS = 6800.0
 NOMINAL_HBM_GBS = 7900.0
 # what the staged step kernel is compiled from, flags included (the capture
@@ -140,6 +141,35 @@ def profiled_traffic(shape):
             prof = json.load(f)
         if prof.get("kernel_src_sha") == kernel_source_hash() and prof.get("shape") == shape:
             return float(prof["dram_bytes_per_launch"])
+    except Exception:
+        pass
+    return None
+
+
+CHAIN_SOURCES = ("paper_2401_14221_gb300/csrc/kf_num.cuh",
+                 "paper_2401_14221_gb300/csrc/kf_device.cuh",
+                 "paper_2401_14221_gb300/csrc/kf_chain.cuh",
+                 "paper_2401_14221_gb300/csrc/kf_chain.cu",
+                 "paper_2401_14221_gb300/build.py")
+
+
+def chain_source_hash():
+    h = hashlib.sha256()
+    for rel in CHAIN_SOURCES:
+        with open(os.path.join(ROOT, rel), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_chain_instructions():
+    """Thread instructions per track-layer of the FP32 fused chain from the
+    committed ncu summary, if taken on the current chain source; else None."""
+    path = os.path.join(ROOT, "profiles", "chain_instructions.json")
+    try:
+        with open(path) as f:
+            prof = json.load(f)
+        if prof.get("kernel_src_sha") == chain_source_hash():
+            return float(prof["instructions_per_track_layer"])
     except Exception:
         pass
     return None
@@ -432,6 +462,13 @@ def chain_bench(args, kf, W, dev, rank):
     ada_fn = lambda: dc.run(kf.KF_ADAPTIVE)
     timed(ada_fn, 2)
     adaptive_ms = timed(ada_fn, reps)
+    # context: the whole chain in double, and with the double-float update
+    f64_fn = lambda: dc.run(kf.KF_FP64)
+    timed(f64_fn, 1)
+    fp64_ms = timed(f64_fn, max(3, reps // 3))
+    df_fn = lambda: dc.run(kf.KF_DF_UPDATE)
+    timed(df_fn, 1)
+    df_ms = timed(df_fn, reps)
     # algorithmic bytes per track: fused reads state, cov, charge once (109 B),
     # hits + hit covariances per layer (36 B each), writes state + cov (108 B);
     # plain launches move 253 B per track per layer
@@ -440,6 +477,18 @@ def chain_bench(args, kf, W, dev, rank):
     # the chain is issue-bound: its roofline is the FP32 arithmetic peak
     fp32_peak = FP32_LANES * 2 * 2.07e9 / 1e12
     achieved = FLOPS_PER_TRACK_LAYER * cw.n * L / (fused_ms * 1e-3) / 1e12
+    # and, as it is issue-bound, against the instruction-issue peak: one warp
+    # instruction per scheduler per cycle, with the instructions per
+    # track-layer of the committed ncu capture of the same kernel source
+    issue = None
+    ipl = profiled_chain_instructions()
+    if ipl is not None:
+        warp_instr_per_s = ipl / 32.0 * cw.n * L / (fused_ms * 1e-3)
+        issue_peak = SMS * 4 * 2.07e9
+        issue = {"instructions_per_track_layer": ipl, "achieved_warp_instr_per_s": warp_instr_per_s,
+                 "peak": issue_peak, "frac": warp_instr_per_s / issue_peak,
+                 "peak_source": "152 SMs x 4 schedulers x 1 warp instruction x 2.07 GHz",
+                 "instructions_source": "profiles/chain_instructions.json (ncu, 64 events)"}
     return {"workload": f"{len(cw.event_sizes)} events, {cw.n} tracks (lognormal sizes, median "
                         f"5000, clipped 500-40000), {L} alternating layers",
             "roofline": {"bound": "alu", "achieved": achieved, "peak": fp32_peak,
@@ -447,12 +496,20 @@ def chain_bench(args, kf, W, dev, rank):
                          "flops_per_track_layer": FLOPS_PER_TRACK_LAYER,
                          "peak_source": "152 SMs x 128 FP32 lanes x 2 flops x 2.07 GHz",
                          "frac_of_hbm": (109 + 36 * L + 108) * cw.n / (fused_ms * 1e-3) / 1e9
-                                        / measured_hbm_peak()[0]},
+                                        / measured_hbm_peak()[0],
+                         "issue": issue},
             "tracks": cw.n, "layers": L,
             "fused_ms": fused_ms, "fused_tracks_per_s": cw.n / (fused_ms * 1e-3),
             "plain_ms": plain_ms, "plain_tracks_per_s": cw.n / (plain_ms * 1e-3),
             "speedup": plain_ms / fused_ms,
             "fused_adaptive_ms": adaptive_ms,
+            "fused_fp64_ms": fp64_ms,
+            "fused_dfloat_update_ms": df_ms,
+            # KF_ADAPTIVE and KF_FP64 meet the accuracy bounds on every track;
+            # FP32 state between layers (all per-layer launches, and the
+            # float-state fused variants) misses them on the ~0.3 % of tracks
+            # that cross a layer at grazing incidence
+            "accurate_fused_vs_plain": plain_ms / adaptive_ms,
             "fused_GBps": fused_b * cw.n / (fused_ms * 1e-3) / 1e9,
             "plain_GBps": plain_b * cw.n / (plain_ms * 1e-3) / 1e9,
             "bytes_per_track": {"fused": fused_b, "plain": plain_b},
@@ -899,10 +956,17 @@ def main():
                                      charge=np.tile(w.charge, 4)[:m], hit=tile(w.hit),
                                      hitcov=tile(w.hitcov))
             bm = [kf.upload(wm, kind, width, dev) for _ in range(4 if mult < 1 else 2)]
+            # each size with the launch shape the library's autotuner picks
+            # for it (the headline's shape suits 960,000 tracks)
+            kf.kf_set_step_kernel(kf.KF_STEP_AUTO)
+            shape = kf.autotune_step(bm[0])
             ms_m = graph_time(bm, reps)
+            kf.kf_set_step_kernel(modes[chosen_kernel])
+            kf.kf_set_staged_ctas_per_sm(3 if chosen_kernel == "staged3" else 2)
             scaling.append({"tracks": m, "ms": ms_m, "tracks_per_s": m / (ms_m * 1e-3),
                             "GBps": BYTES_PER_TRACK_P2R * m / (ms_m * 1e-3) / 1e9,
-                            "frac": BYTES_PER_TRACK_P2R * m / (ms_m * 1e-3) / 1e9 / peak})
+                            "frac": BYTES_PER_TRACK_P2R * m / (ms_m * 1e-3) / 1e9 / peak,
+                            "shape": shape})
             del bm
 
     # Roofline of the step kernel: algorithmic bytes / average launch time.

@@ -125,6 +125,17 @@ __global__ void __launch_bounds__(kThreads, CTAS)
   // --------------------------------------------------------------- compute
   const int il = warp * 32 + lane;
   const int blk = il / W, r = il % W;
+  // charge and the per-track surface, requested one tile ahead so that
+  // their latency hides behind the previous tile's step
+  auto fetch = [&](int64_t k, float &q, float &sf) {
+    int64_t f, mm;
+    sch.tile(k, blockIdx.x, a.n, &f, &mm);
+    const bool lv = il < mm;
+    q = lv ? (float)__ldg(a.charge + f + il) : 1.0f;
+    sf = __ldg(a.surf + ((a.surf_per_track && lv) ? f + il : 0));
+  };
+  float qf_next = 1.0f, surf_next = 0.0f;
+  if (ntiles > 0) fetch(0, qf_next, surf_next);
   for (int64_t k = 0; k < ntiles; ++k) {
     const int s = (int)(k % kStages);
     const uint32_t ph = (uint32_t)(k / kStages) & 1u;
@@ -132,8 +143,8 @@ __global__ void __launch_bounds__(kThreads, CTAS)
     sch.tile(k, blockIdx.x, a.n, &first, &m);
     const int64_t i = first + il;
     const bool live = il < m;
-    const float qf = live ? (float)__ldg(a.charge + i) : 1.0f;
-    const float surf = __ldg(a.surf + ((a.surf_per_track && live) ? i : 0));
+    const float qf = qf_next, surf = surf_next;
+    if (k + 1 < ntiles) fetch(k + 1, qf_next, surf_next);
     if (!mbar_wait(&full[s], ph, err, wait_polls, &abort_flag)) break;
 
     const unsigned char *st = smem + s * kStageB;
@@ -173,9 +184,19 @@ __global__ void __launch_bounds__(kThreads, CTAS)
       }
     }
     stt |= finite_status(p, C);
-    if (!(stt & kNoIntersect)) encode_cov(C, sg, rh);  // else: the input sigma / rho
     const int64_t b6 = (i / W) * (6 * W) + (i % W);
     const int64_t b15 = (i / W) * (15 * W) + (i % W);
+    if (!(stt & kNoIntersect)) {
+      encode_cov(C, sg, rh);
+    } else {
+      // a track that was not propagated gets its input sigma / rho back, bit
+      // for bit: re-read from global memory (rare), so that the staged input
+      // need not stay in registers across the step
+#pragma unroll
+      for (int c = 0; c < 6; ++c) sg[c] = a.sigma_in[b6 + c * W];
+#pragma unroll
+      for (int q = 0; q < 15; ++q) rh[q] = a.rho_in[b15 + q * W];
+    }
 #pragma unroll
     for (int c = 0; c < 6; ++c) __stcs(a.state_out + b6 + c * W, p[c]);
 #pragma unroll
