@@ -115,3 +115,23 @@ def test_device_wait_limit_range(lib):
     kf.kf_set_device_wait_limit(1 << 24)
     kf.kf_set_device_wait_limit(0)
     kf.kf_set_device_wait_limit(-1)
+
+
+def test_binding_constants_match_the_header(lib):
+    # every #define KF_* the binding mirrors carries the header's value
+    import re
+    text = open(kf.HEADER).read()
+    defines = {m.group(1): int(m.group(2), 0)
+               for m in re.finditer(r"#define\s+(KF_[A-Z0-9_]+)\s+([0-9]+)u?\b", text)}
+    names = ["KF_OK", "KF_ERR_ARG", "KF_ERR_CUDA", "KF_ERR_UNSUPPORTED", "KF_ERR_TIMEOUT",
+             "KF_SOA", "KF_AOSOA", "KF_FP32", "KF_FP64_UPDATE", "KF_JOSEPH", "KF_FP64",
+             "KF_ADAPTIVE", "KF_DF_UPDATE", "KF_MAX_LAYERS", "KF_P2Z", "KF_P2R",
+             "KF_NOALLOC_MAX_CHUNK", "KF_STEP_AUTO", "KF_STEP_DIRECT", "KF_STEP_STAGED",
+             "KF_DEVERR_TIMEOUT", "KF_HOST_AUTO", "KF_HOST_COPY", "KF_HOST_DIRECT"]
+    for name in names:
+        assert name in defines, name
+        assert getattr(kf, name) == defines[name], name
+    bits = {"NO_INTERSECT": "KF_NO_INTERSECT", "S_NOT_PD": "KF_S_NOT_PD", "BAD_K": "KF_BAD_K",
+            "NONFINITE": "KF_NONFINITE"}
+    for py, c in bits.items():
+        assert getattr(kf, py) == defines[c], c
