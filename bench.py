@@ -44,8 +44,8 @@ BYTES_PER_TRACK_P2R = 253
 BYTES_PER_TRACK_P2Z = 237
 # FP32 operations per track and layer of the fused chain (FFMA counted twice,
 # FMUL, FADD), from the ncu thread-instruction counters of one chain launch
-# on 64 events (bench.py --profile-only --kind chain, captured with ncu --set full)
-FLOPS_PER_TRACK_LAYER = 465
+# on 64 events (bench.py --profile-only --kind chain; profiles/chain_instructions.json)
+FLOPS_PER_TRACK_LAYER = 502
 # FP32 peak from the unit counts: 152 SMs x 128 FP32 lanes x 2 flops x clock
 SMS = 152
 FP32_LANES = SMS * 128
@@ -139,8 +139,9 @@ def profiled_traffic(shape):
     try:
         with open(path) as f:
             prof = json.load(f)
-        if prof.get("kernel_src_sha") == kernel_source_hash() and prof.get("shape") == shape:
-            return float(prof["dram_bytes_per_launch"])
+        entry = prof.get("shapes", {}).get(shape)
+        if prof.get("kernel_src_sha") == kernel_source_hash() and entry:
+            return float(entry["dram_bytes_per_launch"])
     except Exception:
         pass
     return None
@@ -470,10 +471,12 @@ def chain_bench(args, kf, W, dev, rank):
     timed(df_fn, 1)
     df_ms = timed(df_fn, reps)
     # algorithmic bytes per track: fused reads state, cov, charge once (109 B),
-    # hits + hit covariances per layer (36 B each), writes state + cov (108 B);
-    # plain launches move 253 B per track per layer
-    fused_b = 109 + 36 * L + 108
-    plain_b = 253 * L
+    # per layer the hit and hit covariance a layer measures (a cylinder 36 B,
+    # a plane x, y and their 2x2 covariance: 20 B), writes state + cov
+    # (108 B); plain launches move 253 B (cylinder) or 237 B (plane) per layer
+    hit_b = [36 if k == W.P2R else 20 for k in cw.kinds]
+    fused_b = 109 + sum(hit_b) + 108
+    plain_b = sum(253 if k == W.P2R else 237 for k in cw.kinds)
     # the chain is issue-bound: its roofline is the FP32 arithmetic peak
     fp32_peak = FP32_LANES * 2 * 2.07e9 / 1e12
     achieved = FLOPS_PER_TRACK_LAYER * cw.n * L / (fused_ms * 1e-3) / 1e12
@@ -495,7 +498,7 @@ def chain_bench(args, kf, W, dev, rank):
                          "unit": "TFLOP/s", "frac": achieved / fp32_peak,
                          "flops_per_track_layer": FLOPS_PER_TRACK_LAYER,
                          "peak_source": "152 SMs x 128 FP32 lanes x 2 flops x 2.07 GHz",
-                         "frac_of_hbm": (109 + 36 * L + 108) * cw.n / (fused_ms * 1e-3) / 1e9
+                         "frac_of_hbm": fused_b * cw.n / (fused_ms * 1e-3) / 1e9
                                         / measured_hbm_peak()[0],
                          "issue": issue},
             "tracks": cw.n, "layers": L,
