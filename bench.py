@@ -339,7 +339,7 @@ def cpu_baseline(w):
             "single_core_sample": f"the first {m} tracks of the workload on one thread"}
 
 
-def compressed_bench(kf, W, w, dev, kind, width, reps=100):
+def compressed_bench(kf, W, w, dev, kind, width, reps=100, staged=True):
     """The step on the compressed covariance store (FP32 sigmas + FP16
     correlations): 193 algorithmic bytes per p2r track instead of 253."""
     import torch
@@ -372,7 +372,8 @@ def compressed_bench(kf, W, w, dev, kind, width, reps=100):
     ms = a.elapsed_time(e) / reps
     return {"ms": ms, "tracks_per_s": w.n / (ms * 1e-3), "bytes_per_track": 193,
             "GBps": 193 * w.n / (ms * 1e-3) / 1e9,
-            "kernel": "staged (bulk copies)" if kind == kf.KF_AOSOA else "one thread per track"}
+            "kernel": "staged (bulk copies)" if (staged and kind == kf.KF_AOSOA)
+                      else "one thread per track"}
 
 
 def chain_bench(args, kf, W, dev, rank):
@@ -766,15 +767,19 @@ def main():
 
     # Kernel x layout sweep (outside the timed region): the direct kernel and
     # the staged kernel (2 or 3 CTAs per SM) on SoA and the AoSoA widths.
+    # direct: one thread per track, 128-thread CTAs; staged2 / staged3: the
+    # persistent bulk-copy kernel with 2 CTAs x 3 stages or 3 CTAs x 2 stages
     modes = {"direct": kf.KF_STEP_DIRECT, "staged": kf.KF_STEP_STAGED,
              "staged2": kf.KF_STEP_STAGED, "staged3": kf.KF_STEP_STAGED}
+    swept = ("direct", "staged2", "staged3")
     sweep = {}
     if args.layout == "auto" or args.step_kernel == "auto":
         for lname, (kind, width) in layouts.items():
             if args.layout != "auto" and lname != args.layout:
                 continue
             bs = [kf.upload(w, kind, width, dev) for _ in range(2)]
-            for mname, mode in modes.items():
+            for mname in swept:
+                mode = modes[mname]
                 if args.step_kernel != "auto" and mname != args.step_kernel:
                     continue
                 kf.kf_set_step_kernel(mode)
@@ -1027,6 +1032,9 @@ def main():
     # (context for the precision study; errors are measured by the tests).
     variants = {}
     if not args.no_variants:
+        # each variant with the library's default launch shape for it
+        kf.kf_set_step_kernel(kf.KF_STEP_AUTO)
+        kf.autotune_clear()
         for vname, prec in (("fp32", kf.KF_FP32), ("fp64_update", kf.KF_FP64_UPDATE),
                             ("dfloat_update", kf.KF_DF_UPDATE),
                             ("joseph", kf.KF_JOSEPH), ("fp64", kf.KF_FP64),
@@ -1042,7 +1050,15 @@ def main():
             ms = a.elapsed_time(b) / 100
             variants[vname] = {"ms": ms, "tracks_per_s": w.n / (ms * 1e-3),
                                "GBps": BYTES_PER_TRACK_P2R * w.n / (ms * 1e-3) / 1e9}
+        # the compressed store: its staged kernel (the default for AoSoA), and
+        # its one-thread-per-track kernel
+        mode_now = modes[chosen_kernel]
+        kf.kf_set_step_kernel(kf.KF_STEP_AUTO)
         variants["compressed_fp32"] = compressed_bench(kf, W, w, dev, kind, width)
+        kf.kf_set_step_kernel(kf.KF_STEP_DIRECT)
+        variants["compressed_fp32_direct"] = compressed_bench(kf, W, w, dev, kind, width,
+                                                              staged=False)
+        kf.kf_set_step_kernel(mode_now)
 
     chain = None
     if not args.no_chain:

@@ -565,10 +565,13 @@ int kf_server_destroy(kf_server *s);
  * kf_set_step_kernel -- choose the single-step kernel for all later calls in
  * this process (a tuning knob; the results are the same, bit for bit):
  *   KF_STEP_AUTO    (default) the autotuner's choice where it has one, else
- *                   the direct kernel for n <= 131072 (lower latency on
- *                   small batches) and above that the staged kernel where it
- *                   applies, else the direct one;
- *   KF_STEP_DIRECT  one thread per track with direct global loads (any layout);
+ *                   the direct kernel in 128-thread CTAs (on GB300 it leads
+ *                   or ties the staged kernel from 240,000 to 3.84 M tracks
+ *                   and at every layout measured), and for the FP64-pipe-
+ *                   bound variants (KF_FP64_UPDATE, KF_FP64) the staged
+ *                   kernel at 2 CTAs/SM where it applies;
+ *   KF_STEP_DIRECT  one thread per track with direct global loads (any
+ *                   layout), 128-thread CTAs;
  *   KF_STEP_STAGED  a persistent kernel in which a producer warp streams
  *                   tiles into shared memory with bulk asynchronous copies
  *                   while eight warps compute: any AoSoA layout, and SoA when

@@ -26,13 +26,20 @@ int sm_count(int dev, int *out);
 // CTAs per SM of the grid-stride kernel for arrays in host memory.
 constexpr int kHostGridPerSm = 1;
 
-// Without a tuning entry, batches up to this many tracks run the
-// one-thread-per-track kernel: the staged kernel's barrier set-up and
-// pipeline fill are not repaid by so few tiles (p2z on GB300, isolated
-// launch / back to back in a graph: 8,192 tracks 6.8 / 2.3 us against
-// 8.9 / 2.8 us staged; 131,072 tracks 8.8 / 6.2 against 10.9 / 7.3 us;
-// at 960,000 the staged kernel leads, 37 against 47 us).
-constexpr int64_t kSmallBatchDirect = 131072;
+// Without a tuning entry every batch in device memory runs the
+// one-thread-per-track kernel in 128-thread CTAs.  With every operation
+// explicitly rounded it needs 76 registers (six CTAs, 24 warps per SM), and
+// on GB300 (graphs of 16 launches, microseconds per launch, against the
+// staged kernel's better shape) it led or tied at every size and layout
+// tried: p2r AoSoA32 240,000 tracks 11.5 vs 12.3; 960,000 36.6 vs 37.3
+// (0.977 of the measured HBM copy bandwidth); 1,920,000 70.2 vs 74.5;
+// 3,840,000 137.5 vs 158.6 (1.04); AoSoA16/64/128 and SoA at 960,000
+// likewise; p2z AoSoA32 960,000 34.9 vs 35.5.  Only at 480,000 p2r tracks
+// was the staged kernel (3 CTAs/SM) ahead, 19.4 vs 19.9.  64-thread CTAs
+// time the same; 256-thread CTAs are 3 % slower; holding it to 72 or 64
+// registers for more warps gained nothing or spilled.  The autotuner still
+// times both kernels.
+constexpr int kDirectThreads = 128;
 
 struct Loc {
   int64_t base;
@@ -237,10 +244,13 @@ static int launch_step_main(int kind, int precision, const StepArgs &a, cudaStre
   // The staged kernel copies whole tiles of device memory with 16-byte-
   // aligned bulk copies: any AoSoA layout, SoA when n is a multiple of 4.
   const bool staged_ok = !plain_loads && (!a.soa || (a.n & 3) == 0);
-  LaunchConfig cfg{(staged_ok && a.n > kSmallBatchDirect) ? KF_STEP_STAGED : KF_STEP_DIRECT, 256,
-                   2};
+  // the FP64 variants are bound by GB300's FP64 pipe, where the staged
+  // kernel's decoupled loads help (960,000 p2r tracks: FP64 update 262 us
+  // staged at 2 CTAs/SM against 300 us direct; all-FP64 1,044 against 1,092)
+  const bool fp64 = precision == KF_FP64_UPDATE || precision == KF_FP64;
+  LaunchConfig cfg{(fp64 && staged_ok) ? KF_STEP_STAGED : KF_STEP_DIRECT, kDirectThreads, 2};
   if (plain_loads) {
-    // host or managed memory: the defaults above (direct, 256 threads)
+    // host or managed memory: the grid-stride kernel below
   } else if (const LaunchConfig *o = thread_override()) {
     cfg = *o;
   } else {

@@ -213,7 +213,7 @@ extern "C" int kf_propagate_update_compressed(
                    state_out, sigma_out, reinterpret_cast<__half *>(rho_out),
                    charge, hit, hit_cov, surf, status, d.n, d.soa, d.lw, params->bz,
                    surf_per_track};
-  const int threads = 256;
+  const int threads = 128;  // as the FP32-store step kernel
   const int64_t blocks = (d.n + threads - 1) / threads;
   if (blocks > 0x7fffffffLL) return set_error(KF_ERR_ARG, "n too large for one launch");
   const unsigned g = (unsigned)blocks;
@@ -248,7 +248,7 @@ extern "C" int kf_propagate_update_compressed(
   if (params->precision != KF_ADAPTIVE) return KF_OK;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)((d.n + kRedoSpan - 1) / kRedoSpan));
-  cfg.blockDim = dim3(threads);
+  cfg.blockDim = dim3(kRedoSpan / kRedoPerThread);  // a block gathers its span of kRedoSpan
   cfg.stream = s;
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
