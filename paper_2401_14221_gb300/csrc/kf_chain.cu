@@ -93,8 +93,8 @@ __global__ void __launch_bounds__(256, 3) chain_mark_kernel(const ChainArgs a) {
 // KF_ADAPTIVE's second pass: tracks marked kRedo run the whole chain again
 // from their inputs in double (chain_track_fp64).  Each block gathers the
 // marked tracks of its span first (gather_marked), so warps run full.
-__global__ void __launch_bounds__(256) chain_redo_kernel(const ChainArgs a) {
-  __shared__ int32_t list[kRedoSpan];
+__global__ void __launch_bounds__(kRedoThreads) chain_redo_kernel(const ChainArgs a) {
+  __shared__ uint16_t list[kRedoSpan];
   __shared__ int count;
   const int64_t span0 = (int64_t)blockIdx.x * kRedoSpan;
   const int cnt = gather_marked(a.status, span0, a.n, list, &count);
@@ -190,6 +190,6 @@ extern "C" int kf_kalman_chain(const kf_params *params, kf_layout layout, float 
   }
   if (int rc = check_cuda(cudaGetLastError(), "chain launch")) return rc;
   if (params->precision != KF_ADAPTIVE) return KF_OK;
-  chain_redo_kernel<<<(unsigned)((d.n + kRedoSpan - 1) / kRedoSpan), 256, 0, s>>>(a);
+  chain_redo_kernel<<<(unsigned)((d.n + kRedoSpan - 1) / kRedoSpan), kRedoThreads, 0, s>>>(a);
   return check_cuda(cudaGetLastError(), "chain redo pass launch");
 }

@@ -130,8 +130,8 @@ __global__ void __launch_bounds__(256) step_kernel_strided(const __grid_constant
 // span of kRedoSpan tracks (one 16-byte status load per 16 tracks), then its
 // threads run the FP64 step on them, 32 marked tracks to a warp.
 template <int KIND>
-__global__ void __launch_bounds__(256) redo_pass_kernel(const __grid_constant__ StepArgs a) {
-  __shared__ int32_t list[kRedoSpan];
+__global__ void __launch_bounds__(kRedoThreads) redo_pass_kernel(const __grid_constant__ StepArgs a) {
+  __shared__ uint16_t list[kRedoSpan];
   __shared__ int count;
   // Launched as a programmatic dependent of the step kernel: wait here until
   // it has completed and its status marks are visible.  Before that, let the
@@ -156,7 +156,7 @@ int launch_redo_pass(int kind, const StepArgs &a, cudaStream_t s) {
   // programmatic dependent launch: scheduled while the step kernel drains
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(g);
-  cfg.blockDim = dim3(256);
+  cfg.blockDim = dim3(kRedoThreads);
   cfg.stream = s;
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;

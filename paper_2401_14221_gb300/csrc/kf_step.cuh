@@ -103,26 +103,34 @@ __device__ __forceinline__ unsigned load_status16(const uint8_t *status, int64_t
 }
 
 // Redo passes gather the marked tracks of a span of kRedoSpan tracks into a
-// shared-memory list before running them, so that each warp runs 32 marked
-// tracks instead of one marked track among 31 idle lanes: GB300 issues an
-// FP64 warp instruction over many cycles whether or not its lanes are active.
-constexpr int kRedoPerThread = 32;
-constexpr int kRedoSpan = 256 * kRedoPerThread;  // tracks per 256-thread block
+// shared-memory list before running them, so that each warp runs up to 32
+// marked tracks instead of one marked track among 31 idle lanes: GB300
+// issues an FP64 warp instruction over many cycles whether or not its lanes
+// are active.  A redo block has kRedoThreads threads: the double-precision
+// step takes about 190 registers, and with 64-thread blocks five fit an SM,
+// so every span of a 1.75 M-track chain (214 blocks) is resident at once --
+// the pass is latency-bound (one FP64 warp per scheduler issues on 8 % of
+// cycles), so a second round of blocks would double its time, which
+// 256-thread blocks (one per SM) did.
+constexpr int kRedoSpan = 8192;
+constexpr int kRedoThreads = 64;
 
 // Fill list[0..count) with the offsets (from span0) of the tracks marked
 // kRedo among [span0, min(span0 + kRedoSpan, n)); returns the count.  Every
-// thread of the block must call it.
+// thread of the block must call it; any block size works (each thread
+// scans 16 tracks per 16-byte status load, striding by the block).
 __device__ __forceinline__ int gather_marked(const uint8_t *status, int64_t span0, int64_t n,
-                                             int32_t *list, int *count) {
+                                             uint16_t *list, int *count) {
+  static_assert(kRedoSpan <= 65536, "span offsets are 16-bit");
   if (threadIdx.x == 0) *count = 0;
   __syncthreads();
-  for (int h = 0; h < kRedoPerThread / 16; ++h) {
-    const int64_t base = span0 + ((int64_t)h * blockDim.x + threadIdx.x) * 16;
+  for (int off = threadIdx.x * 16; off < kRedoSpan; off += blockDim.x * 16) {
+    const int64_t base = span0 + off;
     if (base >= n) break;
     uint8_t m[16];
     if (load_status16(status, base, n, m) & kRedo)
       for (int j = 0; j < 16; ++j)
-        if (m[j] & kRedo) list[atomicAdd(count, 1)] = (int32_t)(base - span0 + j);
+        if (m[j] & kRedo) list[atomicAdd(count, 1)] = (uint16_t)(off + j);
   }
   __syncthreads();
   return *count;

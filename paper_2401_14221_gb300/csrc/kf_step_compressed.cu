@@ -120,9 +120,9 @@ __global__ void __launch_bounds__(256)
 // are decoded again from their (untouched) inputs and stepped in FP64.  Each
 // block gathers the marked tracks of its span first, so warps run full.
 template <int KIND>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(kRedoThreads)
     redo_compressed_kernel(const __grid_constant__ CompressedArgs a) {
-  __shared__ int32_t list[kRedoSpan];
+  __shared__ uint16_t list[kRedoSpan];
   __shared__ int count;
   // a programmatic dependent of the step kernel, as the FP32-store redo pass
   asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
@@ -248,7 +248,7 @@ extern "C" int kf_propagate_update_compressed(
   if (params->precision != KF_ADAPTIVE) return KF_OK;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)((d.n + kRedoSpan - 1) / kRedoSpan));
-  cfg.blockDim = dim3(kRedoSpan / kRedoPerThread);  // a block gathers its span of kRedoSpan
+  cfg.blockDim = dim3(kRedoThreads);  // a block gathers its span of kRedoSpan
   cfg.stream = s;
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
