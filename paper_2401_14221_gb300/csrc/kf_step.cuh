@@ -83,23 +83,17 @@ __device__ __forceinline__ unsigned redo_track_fp64(const StepArgs &a, int64_t i
   return st;
 }
 
-// Status bytes base .. base+15 of an [n] array, one 16-byte load where the
-// array is 16-byte aligned and the run is whole, byte loads otherwise.
-__device__ __forceinline__ unsigned load_status16(const uint8_t *status, int64_t base, int64_t n,
-                                                  uint8_t (&m)[16]) {
-  if (base + 16 <= n && (reinterpret_cast<uintptr_t>(status) & 15u) == 0) {
-    const uint4 v = *reinterpret_cast<const uint4 *>(status + base);
-    const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+// Status bytes base .. base+15 of an [n] array as four little-endian words:
+// one 16-byte load where the array is 16-byte aligned and the run is whole,
+// byte loads otherwise (bytes at or past n read as 0).
+__device__ __forceinline__ uint4 load_status16(const uint8_t *status, int64_t base, int64_t n) {
+  if (base + 16 <= n && (reinterpret_cast<uintptr_t>(status) & 15u) == 0)
+    return *reinterpret_cast<const uint4 *>(status + base);
+  uint32_t w[4] = {0u, 0u, 0u, 0u};
 #pragma unroll
-    for (int j = 0; j < 16; ++j) m[j] = (uint8_t)(w[j >> 2] >> (8 * (j & 3)));
-  } else {
-#pragma unroll
-    for (int j = 0; j < 16; ++j) m[j] = base + j < n ? status[base + j] : 0;
-  }
-  unsigned any = 0;
-#pragma unroll
-  for (int j = 0; j < 16; ++j) any |= m[j];
-  return any;
+  for (int j = 0; j < 16; ++j)
+    if (base + j < n) w[j >> 2] |= (uint32_t)status[base + j] << (8 * (j & 3));
+  return make_uint4(w[0], w[1], w[2], w[3]);
 }
 
 // Redo passes gather the marked tracks of a span of kRedoSpan tracks into a
@@ -117,20 +111,31 @@ constexpr int kRedoThreads = 64;
 
 // Fill list[0..count) with the offsets (from span0) of the tracks marked
 // kRedo among [span0, min(span0 + kRedoSpan, n)); returns the count.  Every
-// thread of the block must call it; any block size works (each thread
-// scans 16 tracks per 16-byte status load, striding by the block).
+// thread of the block (kRedoThreads of them) must call it.  Each thread
+// scans kRedoSpan / (16 kRedoThreads) runs of 16 status bytes, striding by
+// the block; all its loads are issued before any is examined, so a span
+// with nothing marked costs one memory latency.
 __device__ __forceinline__ int gather_marked(const uint8_t *status, int64_t span0, int64_t n,
                                              uint16_t *list, int *count) {
+  constexpr int kRuns = kRedoSpan / (16 * kRedoThreads);
+  static_assert(kRuns * 16 * kRedoThreads == kRedoSpan, "whole runs per thread");
   static_assert(kRedoSpan <= 65536, "span offsets are 16-bit");
+  constexpr uint32_t kMarks = 0x01010101u * kRedo;  // the kRedo bit of each byte
   if (threadIdx.x == 0) *count = 0;
-  __syncthreads();
-  for (int off = threadIdx.x * 16; off < kRedoSpan; off += blockDim.x * 16) {
-    const int64_t base = span0 + off;
-    if (base >= n) break;
-    uint8_t m[16];
-    if (load_status16(status, base, n, m) & kRedo)
-      for (int j = 0; j < 16; ++j)
-        if (m[j] & kRedo) list[atomicAdd(count, 1)] = (uint16_t)(off + j);
+  uint4 v[kRuns];
+#pragma unroll
+  for (int r = 0; r < kRuns; ++r) {
+    const int64_t base = span0 + (int64_t)(r * kRedoThreads + threadIdx.x) * 16;
+    v[r] = base < n ? load_status16(status, base, n) : make_uint4(0u, 0u, 0u, 0u);
+  }
+  __syncthreads();  // count is 0
+#pragma unroll
+  for (int r = 0; r < kRuns; ++r) {
+    const uint32_t w[4] = {v[r].x, v[r].y, v[r].z, v[r].w};
+    if (((w[0] | w[1] | w[2] | w[3]) & kMarks) == 0u) continue;
+    const int off = (r * kRedoThreads + threadIdx.x) * 16;
+    for (int j = 0; j < 16; ++j)
+      if ((w[j >> 2] >> (8 * (j & 3))) & kRedo) list[atomicAdd(count, 1)] = (uint16_t)(off + j);
   }
   __syncthreads();
   return *count;
