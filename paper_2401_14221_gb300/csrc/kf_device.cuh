@@ -163,7 +163,9 @@ __device__ __forceinline__ T dsinc_from(T h, T ch, T S) {
 
 // C' = J C J^T for packed symmetric C, with J's structure fixed by NZ/ONE.
 // Loops unroll completely, so every mask test folds at compile time and
-// only the structurally non-zero multiply-adds remain.
+// only the structurally non-zero multiply-adds remain.  A sum over a row of
+// J that has a unit entry starts from that entry's term, so it needs no
+// product.
 template <class T, uint64_t NZ, uint64_t ONE>
 __device__ __forceinline__ void transport(const T (&J)[36], const T (&C)[21], T (&Co)[21]) {
   T M[6][6];  // M = J C
@@ -175,12 +177,17 @@ __device__ __forceinline__ void transport(const T (&J)[36], const T (&C)[21], T 
       bool first = true;
 #pragma unroll
       for (int l = 0; l < 6; ++l) {
-        if ((NZ >> (i * 6 + l)) & 1ull) {
+        if (((NZ & ONE) >> (i * 6 + l)) & 1ull) {
           const T c = C[tri(l, j)];
-          if ((ONE >> (i * 6 + l)) & 1ull)
-            acc = first ? c : add_(acc, c);
-          else
-            acc = first ? mul_(J[i * 6 + l], c) : fma_(J[i * 6 + l], c, acc);
+          acc = first ? c : add_(acc, c);
+          first = false;
+        }
+      }
+#pragma unroll
+      for (int l = 0; l < 6; ++l) {
+        if (((NZ & ~ONE) >> (i * 6 + l)) & 1ull) {
+          const T c = C[tri(l, j)];
+          acc = first ? mul_(J[i * 6 + l], c) : fma_(J[i * 6 + l], c, acc);
           first = false;
         }
       }
@@ -199,11 +206,15 @@ __device__ __forceinline__ void transport(const T (&J)[36], const T (&C)[21], T 
       bool first = true;
 #pragma unroll
       for (int l = 0; l < 6; ++l) {
-        if ((NZ >> (m * 6 + l)) & 1ull) {
-          if ((ONE >> (m * 6 + l)) & 1ull)
-            acc = first ? M[i][l] : add_(acc, M[i][l]);
-          else
-            acc = first ? mul_(M[i][l], J[m * 6 + l]) : fma_(M[i][l], J[m * 6 + l], acc);
+        if (((NZ & ONE) >> (m * 6 + l)) & 1ull) {
+          acc = first ? M[i][l] : add_(acc, M[i][l]);
+          first = false;
+        }
+      }
+#pragma unroll
+      for (int l = 0; l < 6; ++l) {
+        if (((NZ & ~ONE) >> (m * 6 + l)) & 1ull) {
+          acc = first ? mul_(M[i][l], J[m * 6 + l]) : fma_(M[i][l], J[m * 6 + l], acc);
           first = false;
         }
       }
@@ -464,8 +475,8 @@ __device__ __forceinline__ void kalman_update_body(T (&p)[6], T (&C)[21], const 
           const T g0 = fma_(U0[r], G00, mul_(U1[r], G10));
           put(C[tri(i, m)], (c == 0) ? (UNIT0 ? g0 : mul_(g0, ih0))
                                      : fma_(U0[r], G01, mul_(U1[r], G11)));
-        } else {
-          put(C[tri(i, m)], sub_(C[tri(i, m)], fma_(K0[i], U0[m], mul_(K1[i], U1[m]))));
+        } else {  // C' - K0 U0^T - K1 U1^T, two fused steps
+          put(C[tri(i, m)], fma_(neg_(K0[i]), U0[m], fma_(neg_(K1[i]), U1[m], C[tri(i, m)])));
         }
       }
     }
@@ -512,9 +523,8 @@ __device__ __forceinline__ bool kalman_update_f64(float (&p)[6], float (&C)[21],
         const double g0 = __fma_rn((double)U0[r], G00, __dmul_rn((double)U1[r], G10));
         v = (c == 0) ? (UNIT0 ? g0 : __dmul_rn(g0, ih0))
                      : __fma_rn((double)U0[r], G01, __dmul_rn((double)U1[r], G11));
-      } else {
-        v = __dsub_rn((double)C[tri(i, m)],
-                      __fma_rn(K0[i], (double)U0[m], __dmul_rn(K1[i], (double)U1[m])));
+      } else {  // C' - K0 U0^T - K1 U1^T, two fused steps
+        v = __fma_rn(-K0[i], (double)U0[m], __fma_rn(-K1[i], (double)U1[m], (double)C[tri(i, m)]));
       }
       C[tri(i, m)] = (float)v;
     }
