@@ -4,8 +4,9 @@
 // let later launches in KF_STEP_AUTO mode use it.
 //
 // Candidates.  Single step: the one-thread-per-track kernel with 128 or 256
-// threads per CTA, and (AoSoA layouts) the persistent staged kernel with one
-// or two CTAs per SM.  Chain: 64, 128 or 256 threads per CTA.  n buckets are
+// threads per CTA, and (AoSoA layouts, or SoA with n a multiple of 4) the
+// persistent staged kernel with one, two or three CTAs per SM.  Chain: 64,
+// 128 or 256 threads per CTA.  n buckets are
 // powers of two (floor(log2 n)), so one measurement serves batches of
 // similar size.  The cache lives in host memory for the life of the process;
 // kf_autotune_export / kf_autotune_import move it between processes as text.

@@ -68,3 +68,38 @@ def test_chain_autotune_leaves_state(dev):
 def test_import_rejects_malformed_text(dev):
     with pytest.raises(kf.KfError):
         kf.autotune_import("no separators here\n")
+
+
+@pytest.mark.parametrize("width,n", [(128, 77777), (16, 38401), (32, 1000)])
+def test_direct_cta_sizes_equal_bitwise(dev, width, n):
+    # The one-thread-per-track kernel at every CTA size the tuner may pick:
+    # a 64-thread CTA covers half of a 128-wide AoSoA block (its L2 prefetch
+    # asks for the whole block), a 256-thread CTA sixteen 16-wide blocks, and
+    # the last CTA is ragged.  The per-track arithmetic is the same, so the
+    # results are bitwise equal, in place as well.
+    w = W.make_p2r(1, n, seed=63)
+    b = kf.upload(w, kf.KF_AOSOA, width, dev)
+    kf.autotune_clear()
+    kf.autotune_step(b)  # learn this GPU's cache key for the batch
+    fields = kf.autotune_export().splitlines()[0].split("|")
+    outs = []
+    for threads in (64, 128, 256):
+        fields[7], fields[8], fields[9] = str(kf.KF_STEP_DIRECT), str(threads), "0"
+        kf.autotune_clear()
+        kf.autotune_import("|".join(fields) + "\n")
+        b.status.zero_()
+        b.run()
+        outs.append(b.download())
+    kf.autotune_clear()
+    for o in outs[1:]:
+        for x, y in zip(outs[0], o):
+            assert np.array_equal(x, y)
+    fields[8] = "64"
+    kf.autotune_import("|".join(fields) + "\n")
+    b.status.zero_()
+    b.run(in_place=True)
+    kf.autotune_clear()
+    got = (kf.from_device(b.state_in, 6, b.n, b.layout),
+           kf.from_device(b.cov_in, 21, b.n, b.layout), b.status.cpu().numpy())
+    for x, y in zip(outs[0], got):
+        assert np.array_equal(x, y)
