@@ -460,7 +460,9 @@ def chain_bench(args, kf, W, dev, rank):
     plain_fn = plain_graph.replay if plain_graph is not None else dc.run_plain
     timed(plain_fn, 2)
     plain_ms = timed(plain_fn, reps)
-    # the fused chain under KF_ADAPTIVE (FP32, FP64 redo of ill-conditioned layers)
+    # the fused chain under KF_ADAPTIVE (FP32, FP64 redo of ill-conditioned
+    # layers), its CTA size picked by the library's tuner as for FP32
+    ada_tuned = kf.autotune_chain(dc, kf.KF_ADAPTIVE)
     ada_fn = lambda: dc.run(kf.KF_ADAPTIVE)
     timed(ada_fn, 2)
     adaptive_ms = timed(ada_fn, reps)
@@ -468,6 +470,7 @@ def chain_bench(args, kf, W, dev, rank):
     f64_fn = lambda: dc.run(kf.KF_FP64)
     timed(f64_fn, 1)
     fp64_ms = timed(f64_fn, max(3, reps // 3))
+    df_tuned = kf.autotune_chain(dc, kf.KF_DF_UPDATE)
     df_fn = lambda: dc.run(kf.KF_DF_UPDATE)
     timed(df_fn, 1)
     df_ms = timed(df_fn, reps)
@@ -519,7 +522,8 @@ def chain_bench(args, kf, W, dev, rank):
             "bytes_per_track": {"fused": fused_b, "plain": plain_b},
             "fused_launch": "CUDA graph" if fused_graph is not None else "eager",
             "plain_launch": "CUDA graph" if plain_graph is not None else "eager",
-            "autotune": tuned, "layout": chosen,
+            "autotune": tuned, "autotune_adaptive": ada_tuned,
+            "autotune_dfloat_update": df_tuned, "layout": chosen,
             "layout_sweep_ms": layout_sweep,
             "timing": f"median of {reps} runs, CUDA events, state reset outside the timed pair"}
 

@@ -54,8 +54,8 @@ namespace srv {
 
 constexpr int kMaxBatch = 128;
 
-// How long after its last progress the scheduler keeps polling in-flight
-// GPU work without sleeping, microseconds.
+// How long after its last progress the scheduler keeps polling (in-flight
+// GPU work, and new submissions) without sleeping, microseconds.
 constexpr double kSpinUs = 200.0;
 
 // One event of a batch.  Copied events: inputs and outputs are the same
@@ -608,6 +608,13 @@ void scheduler_main(kf_server *s) {
         std::this_thread::yield();
       else
         std::this_thread::sleep_for(std::chrono::microseconds(10));
+      lock.lock();
+    } else if (std::chrono::duration<double, std::micro>(last - progress).count() <
+               kf::srv::kSpinUs) {
+      // idle, but work arrived recently: look for the next submission at
+      // once instead of waiting to be woken (a wake-up costs about 10 us)
+      lock.unlock();
+      std::this_thread::yield();
       lock.lock();
     } else {
       s->cv_work.wait_for(lock, std::chrono::milliseconds(5));
