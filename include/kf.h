@@ -121,11 +121,13 @@ typedef struct {
                                of two floats (about 48 significant bits) with
                                error-free sums and products (Knuth's two-sum,
                                the FMA two-product, the double-word add and
-                               multiply of Joldes, Muller and Popescu 2017).
-                               Same algebra as KF_FP64_UPDATE at FP32
-                               instruction rates (GB300 issues FP64 at 1/64 of
-                               FP32).  In the chain the state is rounded to
-                               FP32 between layers, as for KF_FP64_UPDATE.   */
+                               multiply of Joldes, Muller and Popescu 2017,
+                               compensated two-term dot products after Ogita,
+                               Rump and Oishi 2005).  Same algebra as
+                               KF_FP64_UPDATE at FP32 instruction rates
+                               (GB300 issues FP64 at 1/64 of FP32).  In the
+                               chain the state is rounded to FP32 between
+                               layers, as for KF_FP64_UPDATE.                */
 
 typedef struct {
     float    bz;        /* field along +z in tesla                          */

@@ -533,10 +533,12 @@ __device__ __forceinline__ bool kalman_update_f64(float (&p)[6], float (&C)[21],
 }
 
 // The standard form with S^-1, K and C'' in double-float (kDFUpdate): the
-// same algebra as kalman_update_f64, every product and sum carried as an
-// unevaluated pair of floats (kf_num.cuh), rounded to float once at the end.
-// The float inputs enter exactly: S's determinant and the gain products
-// start from exact two-float products.
+// same algebra as kalman_update_f64, every quantity carried as an
+// unevaluated pair of floats (kf_num.cuh) and rounded to float once at the
+// end.  The float inputs enter exactly: S's determinant starts from exact
+// two-float products, and each two-term sum of products (the gain, G, the
+// posterior elements) is a compensated dot product of the double-word
+// factors and the float inputs (dot2_df).
 template <int SKIP, int M1, bool UNIT0>
 __device__ __forceinline__ bool kalman_update_df(float (&p)[6], float (&C)[21],
                                                  const float (&U0)[6], const float (&U1)[6],
@@ -551,14 +553,14 @@ __device__ __forceinline__ bool kalman_update_df(float (&p)[6], float (&C)[21],
 #pragma unroll
   for (int i = 0; i < 6; ++i) {
     if (i == SKIP) continue;
-    K0[i] = add_dd(mul_df(Si00, U0[i]), mul_df(Si01, U1[i]));
-    K1[i] = add_dd(mul_df(Si01, U0[i]), mul_df(Si11, U1[i]));
-    p[i] = to_float(add_df(add_dd(mul_df(K0[i], r0), mul_df(K1[i], r1)), p[i]));
+    K0[i] = dot2_df(Si00, U0[i], Si01, U1[i]);
+    K1[i] = dot2_df(Si01, U0[i], Si11, U1[i]);
+    p[i] = to_float(add_df(dot2_df(K0[i], r0, K1[i], r1), p[i]));
   }
-  const dfl G00 = add_dd(mul_df(Si00, V00), mul_df(Si01, V01));
-  const dfl G01 = add_dd(mul_df(Si00, V01), mul_df(Si01, V11));
-  const dfl G10 = add_dd(mul_df(Si01, V00), mul_df(Si11, V01));
-  const dfl G11 = add_dd(mul_df(Si01, V01), mul_df(Si11, V11));
+  const dfl G00 = dot2_df(Si00, V00, Si01, V01);
+  const dfl G01 = dot2_df(Si00, V01, Si01, V11);
+  const dfl G10 = dot2_df(Si01, V00, Si11, V01);
+  const dfl G11 = dot2_df(Si01, V01, Si11, V11);
   const dfl ih0 = UNIT0 ? dfl{1.0f, 0.0f} : rcp_d(dfl{h0, 0.0f});
 #pragma unroll
   for (int i = 0; i < 6; ++i) {
@@ -571,13 +573,13 @@ __device__ __forceinline__ bool kalman_update_df(float (&p)[6], float (&C)[21],
       if (mm || im) {
         const int r = mm ? i : m, c = mm ? m : i;  // row r, measured column c
         if (c == 0) {
-          const dfl g0 = add_dd(mul_df(G00, U0[r]), mul_df(G10, U1[r]));
+          const dfl g0 = dot2_df(G00, U0[r], G10, U1[r]);
           v = UNIT0 ? g0 : mul_dd(g0, ih0);
         } else {
-          v = add_dd(mul_df(G01, U0[r]), mul_df(G11, U1[r]));
+          v = dot2_df(G01, U0[r], G11, U1[r]);
         }
       } else {
-        v = add_df(neg_d(add_dd(mul_df(K0[i], U0[m]), mul_df(K1[i], U1[m]))), C[tri(i, m)]);
+        v = sub_dot2_df(C[tri(i, m)], K0[i], U0[m], K1[i], U1[m]);
       }
       C[tri(i, m)] = to_float(v);
     }

@@ -99,6 +99,7 @@ __device__ __forceinline__ bool has_bit_(unsigned st, unsigned b) { return (st &
 //                 <= 4u^2
 //   rcp_d         one Newton-Raphson step x0 + x0 (1 - y x0) from the
 //                 correctly rounded float reciprocal x0 of y's leading part
+//   dot2_df       a x + b y as a compensated dot product (below)
 // Every step is an explicitly rounded float operation, so no compiler
 // contraction can break an error-free transformation.
 struct dfl {
@@ -149,6 +150,35 @@ __device__ __forceinline__ dfl rcp_d(dfl y) {
 }
 // The float nearest to hi + lo.
 __device__ __forceinline__ float to_float(dfl x) { return __fadd_rn(x.hi, x.lo); }
+
+// a x + b y for double-word a, b and floats x, y, as a compensated dot
+// product (the structure of Algorithm Dot2 of Ogita, Rump and Oishi, SIAM
+// J. Sci. Comput. 26 (2005) 1955): the leading products and their sum are
+// error-free (two_prod, two_sum), every rounding error and the low words'
+// products are gathered in one float, and fast_two_sum renormalises.  The
+// error is of order u^2 (|a x| + |b y|): like the double-word sum of the two
+// double-word products (mul_df, add_dd), at about half the instructions.
+__device__ __forceinline__ dfl dot2_df(dfl a, float x, dfl b, float y) {
+  const dfl p = two_prod(a.hi, x), q = two_prod(b.hi, y);
+  const dfl s = two_sum(p.hi, q.hi);
+  float t = __fadd_rn(p.lo, q.lo);
+  t = __fmaf_rn(a.lo, x, t);
+  t = __fmaf_rn(b.lo, y, t);
+  return fast_two_sum(s.hi, __fadd_rn(t, s.lo));
+}
+
+// c - (a x + b y) the same way, with the float c taken into the error-free
+// sum.
+__device__ __forceinline__ dfl sub_dot2_df(float c, dfl a, float x, dfl b, float y) {
+  const dfl p = two_prod(-a.hi, x), q = two_prod(-b.hi, y);
+  const dfl s1 = two_sum(p.hi, q.hi);
+  const dfl s2 = two_sum(s1.hi, c);
+  float t = __fadd_rn(p.lo, q.lo);
+  t = __fmaf_rn(-a.lo, x, t);
+  t = __fmaf_rn(-b.lo, y, t);
+  t = __fadd_rn(t, s1.lo);
+  return fast_two_sum(s2.hi, __fadd_rn(t, s2.lo));
+}
 
 // =============================================================== traits
 // mask_t / stat_t: a comparison's result and a status word of type T;
