@@ -54,6 +54,12 @@ namespace srv {
 
 constexpr int kMaxBatch = 128;
 
+// Tracks per block of the batch grid.  A batch is a few events of a few
+// thousand tracks, and each track's 15 layers are a chain of dependent
+// instructions: 64-thread blocks spread such a batch over four times as many
+// SMs as 256-thread blocks would, so fewer warps share each scheduler.
+constexpr int kBatchThreads = 64;
+
 // How long after its last progress the scheduler keeps polling (in-flight
 // GPU work, and new submissions) without sleeping, microseconds.
 constexpr double kSpinUs = 200.0;
@@ -130,12 +136,12 @@ __global__ void __launch_bounds__(256) batch_chain_kernel(const __grid_constant_
 }
 
 // KF_ADAPTIVE's second pass over a batch.  Block r covers batch-grid blocks
-// [16 r, 16 r + 16) (4,096 track slots, possibly of several events); it
+// [64 r, 64 r + 64) (4,096 track slots, possibly of several events); it
 // gathers the slots whose track is marked kRedo into shared memory, then its
 // threads rerun those tracks' whole chain in double (chain_track_fp64), so
 // that warps run full.  Every event has a status array (the caller's, for a
 // direct event that gave one, else the arena's).
-constexpr int kBatchRedoBlocks = 16;
+constexpr int kBatchRedoBlocks = 64;
 
 __device__ __forceinline__ int batch_event_of(const BatchArgs &a, int64_t b) {
   int lo = 0, hi = a.nev - 1;
@@ -149,17 +155,17 @@ __device__ __forceinline__ int batch_event_of(const BatchArgs &a, int64_t b) {
 
 __global__ void __launch_bounds__(256) batch_redo_kernel(const __grid_constant__ BatchArgs a,
                                                          int64_t nblocks) {
-  __shared__ int16_t ev_of[kBatchRedoBlocks * 256];
-  __shared__ int32_t idx_of[kBatchRedoBlocks * 256];
+  __shared__ int16_t ev_of[kBatchRedoBlocks * kBatchThreads];
+  __shared__ int32_t idx_of[kBatchRedoBlocks * kBatchThreads];
   __shared__ int count;
   if (threadIdx.x == 0) count = 0;
   __syncthreads();
-  for (int h = 0; h < kBatchRedoBlocks; ++h) {
-    const int64_t b = (int64_t)blockIdx.x * kBatchRedoBlocks + h;
+  for (int slot = threadIdx.x; slot < kBatchRedoBlocks * kBatchThreads; slot += blockDim.x) {
+    const int64_t b = (int64_t)blockIdx.x * kBatchRedoBlocks + slot / kBatchThreads;
     if (b >= nblocks) break;
     const int ev = batch_event_of(a, b);
     const EventDesc &e = a.ev[ev];
-    const int64_t i = (b - e.block_begin) * 256 + threadIdx.x;
+    const int64_t i = (b - e.block_begin) * kBatchThreads + slot % kBatchThreads;
     if (i < e.n && (e.status[i] & kRedo)) {
       const int q = atomicAdd(&count, 1);
       ev_of[q] = (int16_t)ev;
@@ -402,7 +408,7 @@ bool launch_batch(kf_server *s, std::vector<Request *> &batch) {
     }
     e.n = r->n;
     e.block_begin = blocks;
-    blocks += (r->n + 255) / 256;
+    blocks += (r->n + kBatchThreads - 1) / kBatchThreads;
   }
   cudaError_t e = cudaSuccess;
   for (Request *r : batch) {
@@ -413,13 +419,13 @@ bool launch_batch(kf_server *s, std::vector<Request *> &batch) {
   if (e == cudaSuccess && blocks > 0) {
     const unsigned g = (unsigned)blocks;
     switch (s->cfg.precision) {
-      case KF_FP32: batch_chain_kernel<kFP32><<<g, 256, 0, s->s_compute>>>(a); break;
-      case KF_FP64_UPDATE: batch_chain_kernel<kFP64Update><<<g, 256, 0, s->s_compute>>>(a); break;
-      case KF_JOSEPH: batch_chain_kernel<kJoseph><<<g, 256, 0, s->s_compute>>>(a); break;
-      case KF_FP64: batch_chain_kernel<kFP64><<<g, 256, 0, s->s_compute>>>(a); break;
-      case KF_DF_UPDATE: batch_chain_kernel<kDFUpdate><<<g, 256, 0, s->s_compute>>>(a); break;
+      case KF_FP32: batch_chain_kernel<kFP32><<<g, kBatchThreads, 0, s->s_compute>>>(a); break;
+      case KF_FP64_UPDATE: batch_chain_kernel<kFP64Update><<<g, kBatchThreads, 0, s->s_compute>>>(a); break;
+      case KF_JOSEPH: batch_chain_kernel<kJoseph><<<g, kBatchThreads, 0, s->s_compute>>>(a); break;
+      case KF_FP64: batch_chain_kernel<kFP64><<<g, kBatchThreads, 0, s->s_compute>>>(a); break;
+      case KF_DF_UPDATE: batch_chain_kernel<kDFUpdate><<<g, kBatchThreads, 0, s->s_compute>>>(a); break;
       default:
-        batch_chain_kernel<kAdaptive><<<g, 256, 0, s->s_compute>>>(a);
+        batch_chain_kernel<kAdaptive><<<g, kBatchThreads, 0, s->s_compute>>>(a);
         e = cudaGetLastError();
         if (e == cudaSuccess)
           batch_redo_kernel<<<(g + kBatchRedoBlocks - 1) / kBatchRedoBlocks, 256, 0, s->s_compute>>>(
