@@ -120,8 +120,10 @@ __device__ __forceinline__ void prefetch_blocks(const float *arr, int64_t i0, in
 // Under AoSoA a CTA that lands on an SM while the previous kernel drains
 // first asks L2 for its inputs -- one bulk prefetch per array of the CTA's
 // whole blocks: the state and covariance, for p2r also the hit and hit
-// covariance (p2z reads only some of their rows) -- so that its loads after
-// the wait find them there instead of in HBM.  A prefetch only moves lines
+// covariance; p2z reads only the first rows of those (x, y and the 2x2
+// covariance), so for p2z one prefetch per block of each covers just those
+// rows -- so that its loads after the wait find them there instead of in
+// HBM.  A prefetch only moves lines
 // into L2, where every SM's loads and stores meet, so it cannot return a
 // value the previous kernel has yet to write.  Measured on GB300, 960,000
 // p2r tracks in graphs of 16 launches: AoSoA 36.6-37.2 -> 35.5 us per
@@ -131,13 +133,29 @@ template <int KIND, int VARIANT>
 __global__ void __launch_bounds__(256) step_kernel(const __grid_constant__ StepArgs a) {
   asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
   const int64_t i0 = (int64_t)blockIdx.x * blockDim.x;
-  if (!a.soa && threadIdx.x == 0) {
+  if (!a.soa) {
     const int64_t i1 = i0 + blockDim.x < a.n ? i0 + blockDim.x : a.n;
-    prefetch_blocks<6>(a.state_in, i0, i1, a.lw);
-    prefetch_blocks<21>(a.cov_in, i0, i1, a.lw);
-    if (KIND == kP2r) {
-      prefetch_blocks<3>(a.hit, i0, i1, a.lw);
-      prefetch_blocks<6>(a.hitcov, i0, i1, a.lw);
+    if (threadIdx.x == 0) {
+      prefetch_blocks<6>(a.state_in, i0, i1, a.lw);
+      prefetch_blocks<21>(a.cov_in, i0, i1, a.lw);
+      if (KIND == kP2r) {
+        prefetch_blocks<3>(a.hit, i0, i1, a.lw);
+        prefetch_blocks<6>(a.hitcov, i0, i1, a.lw);
+      }
+    }
+    if (KIND == kP2z) {
+      // p2z reads the hit's x, y rows and the covariance's xx, xy, yy rows:
+      // the first 2 and 3 rows of each block, one prefetch each per block
+      const int64_t W = int64_t(1) << a.lw, b0 = i0 >> a.lw, nb = ((i1 - 1) >> a.lw) - b0 + 1;
+      if ((int64_t)threadIdx.x < nb) {
+        const int64_t blk = b0 + threadIdx.x;
+        asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(a.hit + blk * 3 * W),
+                     "r"((uint32_t)(2 * W * 4))
+                     : "memory");
+        asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(a.hitcov + blk * 6 * W),
+                     "r"((uint32_t)(3 * W * 4))
+                     : "memory");
+      }
     }
   }
   asm volatile("griddepcontrol.wait;" ::: "memory");
