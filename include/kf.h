@@ -98,8 +98,10 @@ typedef struct {
 #define KF_ADAPTIVE       4 /* FP32, and the whole step redone in FP64 for a
                                track whose FP32 step is ill-conditioned: the
                                hit shrinks a measured variance by more than
-                               1e4, or a cylinder is crossed at an incidence
-                               cosine below 0.2.  There the covariance update
+                               1e4, a cylinder is crossed at an incidence
+                               cosine below 0.3, or the update leaves 1/pT
+                               at or below 0 (a hit far off the track).
+                               There the covariance update
                                C' - K H C' loses more digits than FP32 holds
                                (the propagated covariance is rounded element
                                by element, which breaks the near-perfect

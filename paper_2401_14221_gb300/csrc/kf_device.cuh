@@ -55,9 +55,13 @@ enum Kind : int { kP2z = 0, kP2r = 1 };
 
 // Tracks whose FP32 step is ill-conditioned get an FP64 redo under
 // kAdaptive: a measured variance shrunk by more than kRedoShrink by the hit,
-// or a cylinder crossed at an incidence cosine below kRedoGrazing.
+// a cylinder crossed at an incidence cosine below kRedoGrazing, or an update
+// that leaves 1/pT at or below zero (a hit far off the track, whose update
+// the FP32 rounding no longer resolves).  With a threshold of 0.2 instead
+// of 0.3, tracks crossing the outer barrel layers at cosines of 0.21-0.22
+// missed the covariance bound by up to 27 % in the 15-layer chain.
 constexpr float kRedoShrink = 1e4f;
-constexpr float kRedoGrazing = 0.2f;
+constexpr float kRedoGrazing = 0.3f;
 
 // Constants per lane precision.
 template <class S>
@@ -766,8 +770,9 @@ constexpr unsigned kRedo = 0x80u;
 // The step of a variant on float registers.  kFP32 / kJoseph / kFP64Update
 // / kDFUpdate run in float (with their update form); kFP64 runs every
 // operation in double.  kAdaptive runs in float and, when the step is ill-conditioned (the
-// hit shrinks a measured variance by more than kRedoShrink, or a cylinder is
-// crossed at an incidence cosine below kRedoGrazing), sets kRedo: the caller
+// hit shrinks a measured variance by more than kRedoShrink, a cylinder is
+// crossed at an incidence cosine below kRedoGrazing, or the updated 1/pT is
+// not positive), sets kRedo: the caller
 // then reloads the track's inputs and calls step_in_double -- FP64 where the
 // conditioning demands it, FP32 for everything else, and no register copies
 // of the inputs on the common path.
@@ -789,11 +794,13 @@ __device__ __forceinline__ stat_t<T> step_variant(T (&p)[6], T (&C)[21], T qf, T
     else
       st = p2r_step_t<T, FORM>(p, C, qf, bz, surf, hx, hy, hz, hc, ill, rcos);
     if constexpr (VARIANT == kAdaptive) {
-      // reached, and ill-conditioned or crossed at grazing incidence
+      // reached, and ill-conditioned, crossed at grazing incidence or left
+      // with 1/pT <= 0
       const mask_t<T> reached = not_(has_bit_(st, kNoIntersect));
       const mask_t<T> grazing =
           not_(ge_(abs_(rcos), mul_(cst<T>(kRedoGrazing), surf)));
-      st = st | stat_if<T>(and_(reached, or_(ill, grazing)), kRedo);
+      const mask_t<T> bad_k = has_bit_(st, kBadK);
+      st = st | stat_if<T>(and_(reached, or_(or_(ill, grazing), bad_k)), kRedo);
     }
     return st;
   }

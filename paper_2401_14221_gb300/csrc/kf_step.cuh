@@ -100,13 +100,17 @@ __device__ __forceinline__ uint4 load_status16(const uint8_t *status, int64_t ba
 // shared-memory list before running them, so that each warp runs up to 32
 // marked tracks instead of one marked track among 31 idle lanes: GB300
 // issues an FP64 warp instruction over many cycles whether or not its lanes
-// are active.  A redo block has kRedoThreads threads: the double-precision
-// step takes about 190 registers, and with 64-thread blocks five fit an SM,
-// so every span of a 1.75 M-track chain (214 blocks) is resident at once --
-// the pass is latency-bound (one FP64 warp per scheduler issues on 8 % of
-// cycles), so a second round of blocks would double its time, which
-// 256-thread blocks (one per SM) did.
-constexpr int kRedoSpan = 8192;
+// are active.  The pass is latency-bound (one FP64 warp per scheduler
+// issues on 8 % of cycles), so its time is one warp's chain as long as every
+// marked track runs in the first round: a block has kRedoThreads threads
+// (the double-precision step takes about 190 registers; five 64-thread
+// blocks fit an SM, so the 478 spans of a 1.96 M-track chain are resident
+// at once), and a span is small enough that its marks rarely exceed the
+// block's threads (about 0.6 % of chain tracks are marked: 24 per span on
+// average).  256-thread blocks (one per SM) and 8,192-track spans (48 marks
+// on average, some spans over 64) each took a second round and about
+// doubled the pass.
+constexpr int kRedoSpan = 4096;
 constexpr int kRedoThreads = 64;
 
 // Fill list[0..count) with the offsets (from span0) of the tracks marked
