@@ -169,6 +169,16 @@ def test_precision_study_pt_0p2_to_100(dev, w_prec, precision, step_kernel):
         check(w, b, sample_indices(w.n), VARIANT_FORM[precision])
 
 
+def test_adaptive_step_meets_the_bounds_on_every_track(dev, w_prec):
+    # KF_ADAPTIVE on the whole precision study, 1,000,000 p2z and 1,000,000
+    # p2r tracks with pT from 0.2 to 100 GeV, against the oracle on every
+    # track (the other variants are compared on a sample above)
+    for w in w_prec:
+        b = run(w, dev, (kf.KF_AOSOA, 32), kf.KF_ADAPTIVE)
+        rep = check(w, b, np.arange(w.n))
+        assert rep["n"] == w.n
+
+
 def test_double_float_update_carries_fp64_update_precision(dev, w_prec):
     # KF_DF_UPDATE and KF_FP64_UPDATE share the FP32 propagation and compute
     # S^-1, K and C'' far beyond FP32 (double-float about 48 bits, double 53)
