@@ -7,6 +7,7 @@ exactly.  Full-size workloads run whole on the GPU and are checked on a
 sample that always includes the first and last tracks (the ragged tail).
 """
 import ctypes
+import os
 
 import numpy as np
 import pytest
@@ -164,9 +165,11 @@ def test_p2r_paper_scale_960k(dev, w_p2r, o_p2r_all, layout, step_kernel):
 
 @pytest.mark.parametrize("precision", ALL_VARIANTS)
 def test_precision_study_pt_0p2_to_100(dev, w_prec, precision, step_kernel):
+    # a sample of each million by default; every track with KF_PARITY_FULL=1
+    full = os.environ.get("KF_PARITY_FULL") == "1"
     for w in w_prec:
         b = run(w, dev, (kf.KF_AOSOA, 32), precision)
-        check(w, b, sample_indices(w.n), VARIANT_FORM[precision])
+        check(w, b, np.arange(w.n) if full else sample_indices(w.n), VARIANT_FORM[precision])
 
 
 def test_adaptive_step_meets_the_bounds_on_every_track(dev, w_prec):
