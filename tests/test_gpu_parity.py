@@ -662,7 +662,8 @@ def test_compressed_covariance_step(dev, w_prec, layout):
         else:
             rh = rh.reshape(15, w.n)
         g_cov = W.decompress_cov(g_sig, rh)
-        idx = sample_indices(w.n)
+        # a sample by default; every track with KF_PARITY_FULL=1
+        idx = np.arange(w.n) if os.environ.get("KF_PARITY_FULL") == "1" else sample_indices(w.n)
         c_in = W.decompress_cov(sig, rho)
         o_st, o_cv, o_stat, _ = oracle.step_batch(w.kind, w.state.T[idx], c_in.T[idx],
                                                   w.charge[idx], w.hit.T[idx], w.hitcov.T[idx],
