@@ -350,7 +350,7 @@ def compressed_bench(kf, W, w, dev, kind, width, reps=100, staged=True):
     for _ in range(4):
         st_in = kf.to_device(w.state, lay, dev)
         sg_in = kf.to_device(sig, lay, dev)
-        rh_in = kf.to_device_half(rho, lay, dev)
+        rh_in = kf.to_device_rho(rho, lay, dev)
         bufs.append((st_in, sg_in, rh_in, torch.empty_like(st_in), torch.empty_like(sg_in),
                      torch.empty_like(rh_in), torch.from_numpy(w.charge).to(dev),
                      kf.to_device(w.hit, lay, dev), kf.to_device(w.hitcov, lay, dev),

@@ -269,10 +269,14 @@ int kf_set_host_path(int32_t mode);
  * on a compressed covariance store: per track six FP32 standard deviations
  * sigma_i = sqrt(C_ii) and fifteen FP16 correlations
  * rho_ij = C_ij / (sigma_i sigma_j), stored as IEEE binary16 bit patterns, in
- * packed off-diagonal order (10, 20, 21, 30, 31, 32, 40, ..., 54).
+ * packed off-diagonal order (10, 20, 21, 30, 31, 32, 40, ..., 54: rho_0 .. rho_14).
  *   sigma_in/out   [6 comps] float in the layout
- *   rho_in/out     [15 comps] uint16 in the layout (SoA [15][n]; AoSoA
- *                  [ceil(n/W)][15][W])
+ *   rho_in/out     15 uint16 per track, in pairs: per block of W tracks
+ *                  (AoSoA; SoA is one block of W = n tracks) seven rows of
+ *                  W pairs -- elements 2 (p W + r) and 2 (p W + r) + 1 hold
+ *                  rho_2p and rho_2p+1 of the block's track r, p = 0..6 --
+ *                  then one row of W values rho_14 (element 14 W + r); 15 W
+ *                  values per block, the size of a [15 comps] array
  *   other arguments as for kf_p2z_propagate_update / kf_p2r_propagate_update.
  * The step decodes C_ii = sigma_i^2, C_ij = rho_ij sigma_i sigma_j, runs the
  * FP32 step and encodes the result (sigma = sqrt(max(C_ii, 0)), rho clamped

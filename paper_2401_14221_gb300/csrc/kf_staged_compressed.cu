@@ -3,7 +3,8 @@
 // a persistent CTA whose producer warp streams AoSoA tiles of 256 tracks into
 // shared memory with bulk asynchronous copies (state, sigma, rho, hit, hit
 // covariance: five contiguous runs per tile) while eight compute warps
-// decode, step, encode and store.  The one-thread-per-track kernel reads 193
+// decode, step, encode and store (the correlations in FP16 pairs:
+// kf_compressed.cuh).  The one-thread-per-track kernel reads 193
 // algorithmic bytes per p2r track through 2- and 4-byte loads; staging moves
 // them at the bulk-copy rate.  Arithmetic and results are those of the
 // one-thread-per-track kernel, bit for bit.
@@ -47,12 +48,15 @@ constexpr int kStageB = kStateB + kSigB + kRhoB + kHitB + kHcB;  // 29,184 B
 constexpr int kCompressedCtas = 3;
 constexpr int stages_of(int ctas) { return ctas >= 3 ? 2 : 3; }
 constexpr int smem_of(int ctas) { return stages_of(ctas) * (kStageB + 16); }
+template <int W>
+constexpr int kLog2 = W == 16 ? 4 : W == 32 ? 5 : W == 64 ? 6 : 7;
 
 template <int KIND, int VARIANT, int W, int CTAS>
 __global__ void __launch_bounds__(kThreads, CTAS)
     compressed_staged_kernel(const __grid_constant__ CompressedArgs a, unsigned *err,
                              uint32_t wait_polls) {
   static_assert(kT % W == 0, "tile must hold whole AoSoA blocks");
+  static_assert((1 << kLog2<W>) == W, "AoSoA widths 16, 32, 64, 128");
   constexpr int kStages = stages_of(CTAS);
   extern __shared__ __align__(128) unsigned char smem[];
   uint64_t *full = reinterpret_cast<uint64_t *>(smem + kStages * kStageB);
@@ -154,13 +158,14 @@ __global__ void __launch_bounds__(kThreads, CTAS)
     const float *sht = reinterpret_cast<const float *>(st + kStateB + kSigB + kRhoB);
     const float *shc = reinterpret_cast<const float *>(st + kStateB + kSigB + kRhoB + kHitB);
     float p[6], sg[6], hc[6];
-    __half rh[15];
+    Rho rh;
 #pragma unroll
     for (int c = 0; c < 6; ++c) p[c] = sst[blk * 6 * W + c * W + r];
 #pragma unroll
     for (int c = 0; c < 6; ++c) sg[c] = ssg[blk * 6 * W + c * W + r];
-#pragma unroll
-    for (int q = 0; q < 15; ++q) rh[q] = srh[blk * 15 * W + q * W + r];
+    // the tile is whole AoSoA blocks: its correlations are laid out as in
+    // global memory, from the tile's first block
+    load_rho(srh, RhoLoc{blk * (15 * W / 2) + r, W, blk * (15 * W) + 14 * W + r}, rh);
     const float hx = sht[blk * 3 * W + r];
     const float hy = sht[blk * 3 * W + W + r];
     const float hz = sht[blk * 3 * W + 2 * W + r];
@@ -185,7 +190,7 @@ __global__ void __launch_bounds__(kThreads, CTAS)
     }
     stt |= finite_status(p, C);
     const int64_t b6 = (i / W) * (6 * W) + (i % W);
-    const int64_t b15 = (i / W) * (15 * W) + (i % W);
+    const RhoLoc lr = locate_rho(i, a.n, 0, kLog2<W>);
     if (!(stt & kNoIntersect)) {
       encode_cov(C, sg, rh);
     } else {
@@ -194,15 +199,13 @@ __global__ void __launch_bounds__(kThreads, CTAS)
       // need not stay in registers across the step
 #pragma unroll
       for (int c = 0; c < 6; ++c) sg[c] = a.sigma_in[b6 + c * W];
-#pragma unroll
-      for (int q = 0; q < 15; ++q) rh[q] = a.rho_in[b15 + q * W];
+      load_rho(a.rho_in, lr, rh);
     }
 #pragma unroll
     for (int c = 0; c < 6; ++c) __stcs(a.state_out + b6 + c * W, p[c]);
 #pragma unroll
     for (int c = 0; c < 6; ++c) __stcs(a.sigma_out + b6 + c * W, sg[c]);
-#pragma unroll
-    for (int q = 0; q < 15; ++q) a.rho_out[b15 + q * W] = rh[q];
+    store_rho(a.rho_out, lr, rh);
     if (a.status) a.status[i] = (uint8_t)stt;
   }
 }

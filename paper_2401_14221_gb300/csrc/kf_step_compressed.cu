@@ -1,7 +1,8 @@
 // kf_step_compressed.cu -- the single step on a compressed covariance store:
 // per track six FP32 standard deviations sigma_i = sqrt(C_ii) and fifteen
 // FP16 correlation coefficients rho_ij = C_ij / (sigma_i sigma_j)
-// (off-diagonal entries in packed order 10, 20, 21, 30, ..., 54).
+// (off-diagonal entries in packed order 10, 20, 21, 30, ..., 54, stored in
+// pairs: kf_compressed.cuh).
 //
 // The step is HBM-bound, so a smaller covariance store is a direct speed-up:
 // 24 + 30 = 54 B instead of 84 B per covariance, 193 B instead of 253 B per
@@ -37,15 +38,14 @@ __device__ __forceinline__ Loc locate(int64_t i, int64_t n, int32_t soa, int32_t
 // Load track i: state, and the covariance decoded from sigma / rho.
 template <class T>
 __device__ __forceinline__ void load_compressed(const CompressedArgs &a, const Loc &l6,
-                                                const Loc &l15, T (&p)[6], T (&C)[21]) {
+                                                const RhoLoc &lr, T (&p)[6], T (&C)[21]) {
   float sg[6], Cf[21];
-  __half rh[15];
+  Rho rh;
 #pragma unroll
   for (int c = 0; c < 6; ++c) p[c] = __ldg(a.state_in + l6.base + c * l6.stride);
 #pragma unroll
   for (int c = 0; c < 6; ++c) sg[c] = __ldg(a.sigma_in + l6.base + c * l6.stride);
-#pragma unroll
-  for (int k = 0; k < 15; ++k) rh[k] = a.rho_in[l15.base + k * l15.stride];
+  load_rho(a.rho_in, lr, rh);
   decode_cov(sg, rh, Cf);
 #pragma unroll
   for (int e = 0; e < 21; ++e) C[e] = T(Cf[e]);
@@ -54,24 +54,22 @@ __device__ __forceinline__ void load_compressed(const CompressedArgs &a, const L
 // Encode and store track i's result; a track that was not propagated gets
 // its input sigma / rho back bit for bit.
 __device__ __forceinline__ void store_compressed(const CompressedArgs &a, const Loc &l6,
-                                                 const Loc &l15, const float (&p)[6],
+                                                 const RhoLoc &lr, const float (&p)[6],
                                                  const float (&C)[21], unsigned st) {
   float sg[6];
-  __half rh[15];
+  Rho rh;
   if (!(st & kNoIntersect)) {
     encode_cov(C, sg, rh);
   } else {
 #pragma unroll
     for (int c = 0; c < 6; ++c) sg[c] = __ldg(a.sigma_in + l6.base + c * l6.stride);
-#pragma unroll
-    for (int k = 0; k < 15; ++k) rh[k] = a.rho_in[l15.base + k * l15.stride];
+    load_rho(a.rho_in, lr, rh);
   }
 #pragma unroll
   for (int c = 0; c < 6; ++c) __stcs(a.state_out + l6.base + c * l6.stride, p[c]);
 #pragma unroll
   for (int c = 0; c < 6; ++c) __stcs(a.sigma_out + l6.base + c * l6.stride, sg[c]);
-#pragma unroll
-  for (int k = 0; k < 15; ++k) a.rho_out[l15.base + k * l15.stride] = rh[k];
+  store_rho(a.rho_out, lr, rh);
 }
 
 template <int KIND, int VARIANT>
@@ -80,11 +78,11 @@ __global__ void __launch_bounds__(256)
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= a.n) return;
   const Loc l6 = locate<6>(i, a.n, a.soa, a.lw);
-  const Loc l15 = locate<15>(i, a.n, a.soa, a.lw);
+  const RhoLoc lr = locate_rho(i, a.n, a.soa, a.lw);
   const Loc l3 = locate<3>(i, a.n, a.soa, a.lw);
 
   float p[6], C[21];
-  load_compressed(a, l6, l15, p, C);
+  load_compressed(a, l6, lr, p, C);
   const float qf = (float)__ldg(a.charge + i);
   const float surf = __ldg(a.surf + (a.surf_per_track ? i : 0));
 
@@ -112,7 +110,7 @@ __global__ void __launch_bounds__(256)
     }
   }
   st |= finite_status(p, C);
-  store_compressed(a, l6, l15, p, C, st);
+  store_compressed(a, l6, lr, p, C, st);
   if (a.status) a.status[i] = (uint8_t)st;
 }
 
@@ -132,11 +130,11 @@ __global__ void __launch_bounds__(kRedoThreads)
   for (int q = threadIdx.x; q < cnt; q += blockDim.x) {
     const int64_t i = span0 + list[q];
     const Loc l6 = locate<6>(i, a.n, a.soa, a.lw);
-    const Loc l15 = locate<15>(i, a.n, a.soa, a.lw);
+    const RhoLoc lr = locate_rho(i, a.n, a.soa, a.lw);
     const Loc l3 = locate<3>(i, a.n, a.soa, a.lw);
     double p[6], C[21], hc[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0}, cinc;
     bool shrink;
-    load_compressed(a, l6, l15, p, C);
+    load_compressed(a, l6, lr, p, C);
     constexpr int nhc = KIND == kP2z ? 3 : 6;
 #pragma unroll
     for (int c = 0; c < nhc; ++c) hc[c] = a.hitcov[l6.base + c * l6.stride];
@@ -156,7 +154,7 @@ __global__ void __launch_bounds__(kRedoThreads)
 #pragma unroll
     for (int e = 0; e < 21; ++e) Cf[e] = (float)C[e];
     st |= finite_status(pf, Cf);
-    store_compressed(a, l6, l15, pf, Cf, st);
+    store_compressed(a, l6, lr, pf, Cf, st);
     a.status[i] = (uint8_t)st;
   }
 }

@@ -372,12 +372,17 @@ def kf_propagate_update_compressed(kind, params, layout, state_in, sigma_in, rho
     _check(rc)
 
 
-def to_device_half(a: np.ndarray, layout: kf_layout, device) -> torch.Tensor:
-    """[C, n] float16 SoA -> a flat device tensor in `layout`."""
-    a = np.ascontiguousarray(a, dtype=np.float16)
-    if layout.kind == KF_AOSOA:
-        a = W.to_aosoa(a, layout.width)
-    return torch.from_numpy(a.reshape(-1).copy()).to(device)
+def to_device_rho(rho: np.ndarray, layout: kf_layout, device) -> torch.Tensor:
+    """[15, n] float16 correlations -> the compressed store's rho array in
+    `layout` (FP16 pairs, see kf_propagate_update_compressed) on `device`."""
+    width = layout.width if layout.kind == KF_AOSOA else None
+    return torch.from_numpy(W.rho_to_layout(rho, width).copy()).to(device)
+
+
+def from_device_rho(t: torch.Tensor, n: int, layout: kf_layout) -> np.ndarray:
+    """The compressed store's rho array in `layout` -> [15, n] float16."""
+    width = layout.width if layout.kind == KF_AOSOA else None
+    return W.rho_from_layout(t.cpu().numpy(), n, width)
 
 
 KF_STEP_AUTO, KF_STEP_DIRECT, KF_STEP_STAGED = 0, 1, 2

@@ -478,6 +478,28 @@ def compress_cov(cov: np.ndarray):
     return sig, rho.astype(np.float16)
 
 
+def rho_to_layout(rho: np.ndarray, width=None) -> np.ndarray:
+    """[15, n] FP16 correlations -> the flat rho array of the compressed store.
+    Per block of `width` tracks (width None: SoA, one block of n tracks) seven
+    rows of pairs, element 2 r + h of row p holding track r's rho_{2p+h}, then
+    one row of rho_14: 15 * width values per block."""
+    rho = np.asarray(rho, dtype=np.float16)
+    blocks = rho[None] if width is None else to_aosoa(rho, width)  # [nb, 15, w]
+    nb, _, w = blocks.shape
+    pairs = blocks[:, :14].reshape(nb, 7, 2, w).transpose(0, 1, 3, 2).reshape(nb, 14 * w)
+    return np.ascontiguousarray(np.concatenate([pairs, blocks[:, 14]], axis=1)).reshape(-1)
+
+
+def rho_from_layout(flat: np.ndarray, n: int, width=None) -> np.ndarray:
+    """Inverse of rho_to_layout: the flat rho array -> [15, n]."""
+    w = n if width is None else width
+    nb = 1 if width is None else aosoa_blocks(n, width)
+    b = np.asarray(flat, dtype=np.float16).reshape(nb, 15 * w)
+    pairs = b[:, :14 * w].reshape(nb, 7, w, 2).transpose(0, 1, 3, 2).reshape(nb, 14, w)
+    blocks = np.concatenate([pairs, b[:, None, 14 * w:]], axis=1)
+    return np.ascontiguousarray(blocks[0]) if width is None else from_aosoa(blocks, n)
+
+
 def decompress_cov(sig: np.ndarray, rho: np.ndarray) -> np.ndarray:
     """(sigma [6, n], rho [15, n]) -> [21, n] packed covariance in float64."""
     s = np.asarray(sig, dtype=np.float64)

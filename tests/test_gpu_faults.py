@@ -83,7 +83,7 @@ def test_compressed_staged_wait_runs_out_and_the_context_recovers(dev):
     lay = kf.make_layout(kf.KF_AOSOA, 32, w.n)
     sig, rho = W.compress_cov(w.cov)
     ins = (kf.to_device(w.state, lay, dev), kf.to_device(sig, lay, dev),
-           kf.to_device_half(rho, lay, dev))
+           kf.to_device_rho(rho, lay, dev))
     rest = (torch.from_numpy(w.charge).to(dev), kf.to_device(w.hit, lay, dev),
             kf.to_device(w.hitcov, lay, dev),
             torch.tensor([w.surf], dtype=torch.float32, device=dev))

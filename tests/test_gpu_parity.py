@@ -645,7 +645,7 @@ def test_compressed_covariance_step(dev, w_prec, layout):
         sig, rho = W.compress_cov(w.cov)
         st_in = kf.to_device(w.state, lay, dev)
         sg_in = kf.to_device(sig, lay, dev)
-        rh_in = kf.to_device_half(rho, lay, dev)
+        rh_in = kf.to_device_rho(rho, lay, dev)
         st_out, sg_out, rh_out = torch.empty_like(st_in), torch.empty_like(sg_in), torch.empty_like(rh_in)
         status = torch.zeros(w.n, dtype=torch.uint8, device=dev)
         kind = kf.KF_P2Z if w.kind == W.P2Z else kf.KF_P2R
@@ -656,11 +656,7 @@ def test_compressed_covariance_step(dev, w_prec, layout):
         torch.cuda.synchronize()
         g_st = kf.from_device(st_out, 6, w.n, lay)
         g_sig = kf.from_device(sg_out, 6, w.n, lay)
-        rh = rh_out.cpu().numpy()
-        if lay.kind == kf.KF_AOSOA:
-            rh = W.from_aosoa(rh.reshape(W.aosoa_blocks(w.n, lay.width), 15, lay.width), w.n)
-        else:
-            rh = rh.reshape(15, w.n)
+        rh = kf.from_device_rho(rh_out, w.n, lay)
         g_cov = W.decompress_cov(g_sig, rh)
         # a sample by default; every track with KF_PARITY_FULL=1
         idx = np.arange(w.n) if os.environ.get("KF_PARITY_FULL") == "1" else sample_indices(w.n)
@@ -678,7 +674,7 @@ def run_compressed(w, dev, layout, precision, in_place=False):
     sig, rho = W.compress_cov(w.cov)
     st_in = kf.to_device(w.state, lay, dev)
     sg_in = kf.to_device(sig, lay, dev)
-    rh_in = kf.to_device_half(rho, lay, dev)
+    rh_in = kf.to_device_rho(rho, lay, dev)
     if in_place:
         st_out, sg_out, rh_out = st_in, sg_in, rh_in
     else:
@@ -695,11 +691,7 @@ def run_compressed(w, dev, layout, precision, in_place=False):
     torch.cuda.synchronize()
     g_st = kf.from_device(st_out, 6, w.n, lay)
     g_sig = kf.from_device(sg_out, 6, w.n, lay)
-    rh = rh_out.cpu().numpy()
-    if lay.kind == kf.KF_AOSOA:
-        rh = W.from_aosoa(rh.reshape(W.aosoa_blocks(w.n, lay.width), 15, lay.width), w.n)
-    else:
-        rh = rh.reshape(15, w.n)
+    rh = kf.from_device_rho(rh_out, w.n, lay)
     return g_st, W.decompress_cov(g_sig, rh), status.cpu().numpy()
 
 

@@ -37,6 +37,28 @@ def test_aosoa_round_trip_and_padding():
             assert blocks[i // width, 5, i % width] == a[5, i]
 
 
+def test_rho_pair_layout_round_trip_and_addresses():
+    # the compressed store's correlations: per block of W tracks, pair p of
+    # track r at FP16 elements 2 (p W + r) and 2 (p W + r) + 1 (rho_2p low),
+    # rho_14 at 14 W + r; SoA is one block of n tracks; 15 W values per block
+    rng = np.random.default_rng(5)
+    for n in (1, 7, 31, 32, 33, 1000):
+        rho = rng.uniform(-1, 1, (15, n)).astype(np.float16)
+        for width in (None, 16, 32, 64, 128):
+            flat = W.rho_to_layout(rho, width)
+            w = n if width is None else width
+            nb = 1 if width is None else W.aosoa_blocks(n, width)
+            assert flat.dtype == np.float16 and flat.shape == (nb * 15 * w,)
+            assert np.array_equal(W.rho_from_layout(flat, n, width), rho)
+            for i in (0, n // 2, n - 1):
+                b, r = (0, i) if width is None else (i // width, i % width)
+                base = b * 15 * w
+                for p in range(7):
+                    assert flat[base + 2 * (p * w + r)] == rho[2 * p, i]
+                    assert flat[base + 2 * (p * w + r) + 1] == rho[2 * p + 1, i]
+                assert flat[base + 14 * w + r] == rho[14, i]
+
+
 def test_chain_layers_alternate_and_event_sizes_clip():
     kinds, pos = W.chain_layers()
     assert len(kinds) == 15 and list(kinds[:4]) == [W.P2R, W.P2Z, W.P2R, W.P2Z]
