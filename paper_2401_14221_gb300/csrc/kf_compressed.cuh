@@ -75,11 +75,12 @@ __device__ __forceinline__ void load_rho(const __half *rho, const RhoLoc &l, Rho
   rh.last = rho[l.last];
 }
 
+// streaming stores, as the kernels' other outputs
 __device__ __forceinline__ void store_rho(__half *rho, const RhoLoc &l, const Rho &rh) {
   __half2 *w = reinterpret_cast<__half2 *>(rho);
 #pragma unroll
-  for (int p = 0; p < 7; ++p) w[l.word + p * l.stride] = rh.pr[p];
-  rho[l.last] = rh.last;
+  for (int p = 0; p < 7; ++p) __stcs(w + l.word + p * l.stride, rh.pr[p]);
+  __stcs(rho + l.last, rh.last);
 }
 
 // C_ii = sigma_i^2, C_ij = rho_ij sigma_i sigma_j (FP32).  Each product is

@@ -48,15 +48,13 @@ constexpr int kStageB = kStateB + kSigB + kRhoB + kHitB + kHcB;  // 29,184 B
 constexpr int kCompressedCtas = 3;
 constexpr int stages_of(int ctas) { return ctas >= 3 ? 2 : 3; }
 constexpr int smem_of(int ctas) { return stages_of(ctas) * (kStageB + 16); }
-template <int W>
-constexpr int kLog2 = W == 16 ? 4 : W == 32 ? 5 : W == 64 ? 6 : 7;
 
 template <int KIND, int VARIANT, int W, int CTAS>
 __global__ void __launch_bounds__(kThreads, CTAS)
     compressed_staged_kernel(const __grid_constant__ CompressedArgs a, unsigned *err,
                              uint32_t wait_polls) {
   static_assert(kT % W == 0, "tile must hold whole AoSoA blocks");
-  static_assert((1 << kLog2<W>) == W, "AoSoA widths 16, 32, 64, 128");
+  static_assert(W % 2 == 0, "pairs of correlation rows per block");
   constexpr int kStages = stages_of(CTAS);
   extern __shared__ __align__(128) unsigned char smem[];
   uint64_t *full = reinterpret_cast<uint64_t *>(smem + kStages * kStageB);
@@ -129,26 +127,34 @@ __global__ void __launch_bounds__(kThreads, CTAS)
   // --------------------------------------------------------------- compute
   const int il = warp * 32 + lane;
   const int blk = il / W, r = il % W;
-  // charge and the per-track surface, requested one tile ahead so that
-  // their latency hides behind the previous tile's step
-  auto fetch = [&](int64_t k, float &q, float &sf) {
-    int64_t f, mm;
-    sch.tile(k, blockIdx.x, a.n, &f, &mm);
-    const bool lv = il < mm;
-    q = lv ? (float)__ldg(a.charge + f + il) : 1.0f;
-    sf = __ldg(a.surf + ((a.surf_per_track && lv) ? f + il : 0));
-  };
+  // this thread's track within a tile of whole AoSoA blocks: its elements
+  // sit at these offsets from the tile's start, in shared memory as in
+  // global memory (the tile's first track, a multiple of W, times the
+  // components per track)
+  const int o6 = blk * 6 * W + r, o3 = blk * 3 * W + r;
+  const RhoLoc orh{blk * (15 * W / 2) + r, W, blk * (15 * W) + 14 * W + r};
+  // the next tile's first track and size, with its charge and per-track
+  // surface requested one tile ahead so that their latency hides behind the
+  // previous tile's step
+  int64_t first_next = 0;
+  int m_next = 0;
   float qf_next = 1.0f, surf_next = 0.0f;
-  if (ntiles > 0) fetch(0, qf_next, surf_next);
+  auto fetch = [&](int64_t k) {
+    int64_t mm;
+    sch.tile(k, blockIdx.x, a.n, &first_next, &mm);
+    m_next = (int)mm;
+    const bool lv = il < m_next;
+    qf_next = lv ? (float)__ldg(a.charge + first_next + il) : 1.0f;
+    surf_next = __ldg(a.surf + ((a.surf_per_track && lv) ? first_next + il : 0));
+  };
+  if (ntiles > 0) fetch(0);
   for (int64_t k = 0; k < ntiles; ++k) {
     const int s = (int)(k % kStages);
     const uint32_t ph = (uint32_t)(k / kStages) & 1u;
-    int64_t first, m;
-    sch.tile(k, blockIdx.x, a.n, &first, &m);
-    const int64_t i = first + il;
-    const bool live = il < m;
+    const int64_t first = first_next;
+    const bool live = il < m_next;
     const float qf = qf_next, surf = surf_next;
-    if (k + 1 < ntiles) fetch(k + 1, qf_next, surf_next);
+    if (k + 1 < ntiles) fetch(k + 1);
     if (!mbar_wait(&full[s], ph, err, wait_polls, &abort_flag)) break;
 
     const unsigned char *st = smem + s * kStageB;
@@ -160,20 +166,19 @@ __global__ void __launch_bounds__(kThreads, CTAS)
     float p[6], sg[6], hc[6];
     Rho rh;
 #pragma unroll
-    for (int c = 0; c < 6; ++c) p[c] = sst[blk * 6 * W + c * W + r];
+    for (int c = 0; c < 6; ++c) p[c] = sst[o6 + c * W];
 #pragma unroll
-    for (int c = 0; c < 6; ++c) sg[c] = ssg[blk * 6 * W + c * W + r];
-    // the tile is whole AoSoA blocks: its correlations are laid out as in
-    // global memory, from the tile's first block
-    load_rho(srh, RhoLoc{blk * (15 * W / 2) + r, W, blk * (15 * W) + 14 * W + r}, rh);
-    const float hx = sht[blk * 3 * W + r];
-    const float hy = sht[blk * 3 * W + W + r];
-    const float hz = sht[blk * 3 * W + 2 * W + r];
+    for (int c = 0; c < 6; ++c) sg[c] = ssg[o6 + c * W];
+    load_rho(srh, orh, rh);
+    const float hx = sht[o3];
+    const float hy = sht[o3 + W];
+    const float hz = sht[o3 + 2 * W];
 #pragma unroll
-    for (int c = 0; c < 6; ++c) hc[c] = shc[blk * 6 * W + c * W + r];
+    for (int c = 0; c < 6; ++c) hc[c] = shc[o6 + c * W];
     __syncwarp();
     if (lane == 0) mbar_arrive(&empty[s]);  // stage may be refilled
     if (!live) continue;
+    const int64_t i = first + il;
 
     float C[21];
     decode_cov(sg, rh, C);
@@ -189,8 +194,8 @@ __global__ void __launch_bounds__(kThreads, CTAS)
       }
     }
     stt |= finite_status(p, C);
-    const int64_t b6 = (i / W) * (6 * W) + (i % W);
-    const RhoLoc lr = locate_rho(i, a.n, 0, kLog2<W>);
+    const int64_t b6 = first * 6 + o6;
+    const RhoLoc lr{(first >> 1) * 15 + orh.word, W, first * 15 + orh.last};
     if (!(stt & kNoIntersect)) {
       encode_cov(C, sg, rh);
     } else {

@@ -734,6 +734,39 @@ def test_compressed_staged_equals_direct_bitwise(dev, kind, precision):
         assert np.array_equal(x, y)
 
 
+@pytest.mark.parametrize("width", [16, 32, 128])
+def test_compressed_staged_equals_direct_bitwise_every_width(dev, width):
+    # the staged kernel addresses a tile's correlation pairs from the tile's
+    # first block, the one-thread-per-track kernel from the track index:
+    # the same bits at every AoSoA width (ragged n)
+    w = grazing_p2r(seed=73, n=20011)
+    lay = (kf.KF_AOSOA, width)
+    kf.kf_set_step_kernel(kf.KF_STEP_AUTO)
+    staged = run_compressed(w, dev, lay, kf.KF_FP32)
+    kf.kf_set_step_kernel(kf.KF_STEP_DIRECT)
+    try:
+        direct = run_compressed(w, dev, lay, kf.KF_FP32)
+    finally:
+        kf.kf_set_step_kernel(kf.KF_STEP_AUTO)
+    for x, y in zip(staged, direct):
+        assert np.array_equal(x, y)
+
+
+@pytest.mark.parametrize("layout", [(kf.KF_SOA, 0), (kf.KF_AOSOA, 16), (kf.KF_AOSOA, 128)])
+def test_compressed_ragged_against_the_oracle(dev, layout):
+    # an odd track count: SoA pair rows of odd length, a last AoSoA block
+    # mostly padding; every track against the oracle on the decoded input
+    w = W.make_p2r(1, 4099, seed=74, pt_range=(0.2, 100.0))
+    g = run_compressed(w, dev, layout, kf.KF_FP32)
+    sig, rho = W.compress_cov(w.cov)
+    c_in = W.decompress_cov(sig, rho)
+    o_st, o_cv, o_stat, _ = oracle.step_batch(w.kind, w.state.T, c_in.T, w.charge, w.hit.T,
+                                              w.hitcov.T, w.surf, w.bz, threads=8)
+    rep = compare.compare(g[0].T, g[1].T, g[2], o_st, o_cv, o_stat,
+                          on_cylinder=cylinder_frame(w, o_stat))
+    parity_log.expect_ok("step", rep)
+
+
 def test_prepared_step_equals_the_plain_call(dev):
     # the binding's prepared call marshals the arguments once; the launches
     # are the same calls, so the results are the same bits, on the current
