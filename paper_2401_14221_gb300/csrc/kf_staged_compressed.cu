@@ -135,17 +135,20 @@ __global__ void __launch_bounds__(kThreads, CTAS)
   const RhoLoc orh{blk * (15 * W / 2) + r, W, blk * (15 * W) + 14 * W + r};
   // the next tile's first track and size, with its charge and per-track
   // surface requested one tile ahead so that their latency hides behind the
-  // previous tile's step
+  // previous tile's step.  Nothing consumes the loaded values before that
+  // step (a thread past the tile's end loads the last track's, unused), so
+  // the warp does not wait for them here.
   int64_t first_next = 0;
   int m_next = 0;
-  float qf_next = 1.0f, surf_next = 0.0f;
+  int8_t q_next = 1;
+  float surf_next = 0.0f;
   auto fetch = [&](int64_t k) {
     int64_t mm;
     sch.tile(k, blockIdx.x, a.n, &first_next, &mm);
     m_next = (int)mm;
-    const bool lv = il < m_next;
-    qf_next = lv ? (float)__ldg(a.charge + first_next + il) : 1.0f;
-    surf_next = __ldg(a.surf + ((a.surf_per_track && lv) ? first_next + il : 0));
+    const int64_t j = il < m_next ? first_next + il : a.n - 1;
+    q_next = __ldg(a.charge + j);
+    surf_next = __ldg(a.surf + (a.surf_per_track ? j : 0));
   };
   if (ntiles > 0) fetch(0);
   for (int64_t k = 0; k < ntiles; ++k) {
@@ -153,7 +156,8 @@ __global__ void __launch_bounds__(kThreads, CTAS)
     const uint32_t ph = (uint32_t)(k / kStages) & 1u;
     const int64_t first = first_next;
     const bool live = il < m_next;
-    const float qf = qf_next, surf = surf_next;
+    const int8_t q = q_next;
+    const float surf = surf_next;
     if (k + 1 < ntiles) fetch(k + 1);
     if (!mbar_wait(&full[s], ph, err, wait_polls, &abort_flag)) break;
 
@@ -179,6 +183,7 @@ __global__ void __launch_bounds__(kThreads, CTAS)
     if (lane == 0) mbar_arrive(&empty[s]);  // stage may be refilled
     if (!live) continue;
     const int64_t i = first + il;
+    const float qf = (float)q;
 
     float C[21];
     decode_cov(sg, rh, C);
