@@ -752,11 +752,13 @@ def test_compressed_staged_equals_direct_bitwise_every_width(dev, width):
         assert np.array_equal(x, y)
 
 
+@pytest.mark.parametrize("n", [1, 129, 4099])
 @pytest.mark.parametrize("layout", [(kf.KF_SOA, 0), (kf.KF_AOSOA, 16), (kf.KF_AOSOA, 128)])
-def test_compressed_ragged_against_the_oracle(dev, layout):
-    # an odd track count: SoA pair rows of odd length, a last AoSoA block
-    # mostly padding; every track against the oracle on the decoded input
-    w = W.make_p2r(1, 4099, seed=74, pt_range=(0.2, 100.0))
+def test_compressed_ragged_against_the_oracle(dev, layout, n):
+    # odd track counts: SoA pair rows of odd length, a last AoSoA block
+    # mostly padding, a single track; every track against the oracle on the
+    # decoded input
+    w = W.make_p2r(1, n, seed=74, pt_range=(0.2, 100.0))
     g = run_compressed(w, dev, layout, kf.KF_FP32)
     sig, rho = W.compress_cov(w.cov)
     c_in = W.decompress_cov(sig, rho)
@@ -765,6 +767,37 @@ def test_compressed_ragged_against_the_oracle(dev, layout):
     rep = compare.compare(g[0].T, g[1].T, g[2], o_st, o_cv, o_stat,
                           on_cylinder=cylinder_frame(w, o_stat))
     parity_log.expect_ok("step", rep)
+
+
+def test_compressed_bad_arguments_are_refused(dev):
+    # a correlation array 4 bytes off the 16-byte rule, and an output that
+    # partially overlaps its input, are refused on the host before a launch
+    w = W.make_p2r(1, 1000, seed=15)
+    lay = kf.make_layout(kf.KF_AOSOA, 32, w.n)
+    sig, rho = W.compress_cov(w.cov)
+    rh = kf.to_device_rho(rho, lay, dev)
+    big = torch.zeros(2 * rh.numel(), dtype=torch.float16, device=dev)
+    big[:rh.numel()] = rh
+    st_in, sg_in = kf.to_device(w.state, lay, dev), kf.to_device(sig, lay, dev)
+    st_out, sg_out = torch.empty_like(st_in), torch.empty_like(sg_in)
+    rest = [torch.from_numpy(w.charge).to(dev), kf.to_device(w.hit, lay, dev),
+            kf.to_device(w.hitcov, lay, dev), torch.tensor([w.surf], device=dev)]
+    p = kf.make_params(w.bz)
+
+    def call(rho_in, rho_out):
+        ptrs = [st_in, sg_in, rho_in, st_out, sg_out, rho_out, *rest]
+        return kf.load().kf_propagate_update_compressed(
+            kf.KF_P2R, ctypes.byref(p), lay, *[t.data_ptr() for t in ptrs], 0, None,
+            torch.cuda.current_stream().cuda_stream)
+
+    n = rh.numel()
+    assert call(big[2:2 + n], big[n:]) == kf.KF_ERR_ARG   # 4 bytes off alignment
+    assert "aligned" in kf.kf_last_error_string()
+    assert call(big[:n], big[8:8 + n]) == kf.KF_ERR_ARG   # 16 bytes into the input
+    assert "overlap" in kf.kf_last_error_string()
+    assert call(big[:n], big[n:]) == kf.KF_OK
+    torch.cuda.synchronize()
+    assert kf.kf_take_device_error() == 0
 
 
 def test_prepared_step_equals_the_plain_call(dev):
