@@ -12,12 +12,19 @@
 // kind is uniform across the grid, so the p2z / p2r branch never diverges.
 #include <cuda_runtime.h>
 
+#include <cstdint>
+#include <mutex>
+
 #include "kf_common.cuh"
 #include "kf_device.cuh"
 #include "kf_step.cuh"
 #include "kf_chain.cuh"
 
 namespace kf {
+namespace staged {
+// SM count of a device (cached; kf_step_staged.cu)
+int sm_count(int dev, int *out);
+}  // namespace staged
 
 struct ChainArgs {
   float *state;
@@ -90,30 +97,123 @@ __global__ void __launch_bounds__(256, 3) chain_mark_kernel(const ChainArgs a) {
   if (i < a.n) chain_one<kAdaptive>(a, i);
 }
 
-// KF_ADAPTIVE's second pass: tracks marked kRedo run the whole chain again
-// from their inputs in double (chain_track_fp64).  Each block gathers the
-// marked tracks of its span first (gather_marked), so warps run full.
+// KF_ADAPTIVE's second pass for one marked track: the whole chain again
+// from its (untouched) inputs, in double (chain_track_fp64).
+__device__ __forceinline__ void chain_redo_track(const ChainArgs &a, int64_t i) {
+  const ChainLoc l6 = chain_locate<6>(i, a.n, a.soa, a.lw);
+  const ChainLoc l21 = chain_locate<21>(i, a.n, a.soa, a.lw);
+  const ChainLoc l3 = chain_locate<3>(i, a.n, a.soa, a.lw);
+  float p[6], C[21];
+  for (int c = 0; c < 6; ++c) p[c] = a.state[l6.base + c * l6.stride];
+  for (int e = 0; e < 21; ++e) C[e] = a.cov[l21.base + e * l21.stride];
+  const float qf = (float)a.charge[i];
+  unsigned st = chain_track_fp64(p, C, qf, a.bz, a.L, a.kinds, a.pos, a.hits, a.hit_stride,
+                                 a.hitcovs, a.hc_stride, l3, l6);
+  st |= finite_status(p, C);
+  for (int c = 0; c < 6; ++c) a.state[l6.base + c * l6.stride] = p[c];
+  for (int e = 0; e < 21; ++e) a.cov[l21.base + e * l21.stride] = C[e];
+  a.status[i] = (uint8_t)st;
+}
+
+// The second pass over one list of the whole batch's marked tracks, 32 to
+// a warp.  An FP64 warp instruction occupies the FP64 pipe as long with one
+// lane active as with 32 (spreading a span's marks over two warps instead
+// of one made the adaptive chain slower, 0.761 -> 0.795 ms), so full warps
+// need about a quarter fewer FP64 warp instructions than one partly filled
+// warp per span; one-warp blocks, four per SM, spread them over the SMs.
+// chain_compact_kernel builds the list: each block gathers its span's marks
+// and appends them (one atomic per block; the order of the list varies from
+// run to run, the result of each track does not).
+__global__ void __launch_bounds__(kRedoThreads) chain_compact_kernel(const uint8_t *status,
+                                                                     int64_t n,
+                                                                     uint32_t *count,
+                                                                     uint32_t *list) {
+  __shared__ uint16_t span_list[kRedoSpan];
+  __shared__ int span_count;
+  __shared__ uint32_t base;
+  const int64_t span0 = (int64_t)blockIdx.x * kRedoSpan;
+  const int cnt = gather_marked(status, span0, n, span_list, &span_count);
+  if (cnt == 0) return;  // the same count in every thread of the block
+  if (threadIdx.x == 0) base = atomicAdd(count, (uint32_t)cnt);
+  __syncthreads();
+  for (int q = threadIdx.x; q < cnt; q += blockDim.x)
+    list[base + q] = (uint32_t)(span0 + span_list[q]);
+}
+
+constexpr int kRedoListBlocksPerSm = 4;
+
+__global__ void __launch_bounds__(32) chain_redo_list_kernel(const ChainArgs a,
+                                                             const uint32_t *count,
+                                                             const uint32_t *list) {
+  const int64_t total = *count;
+  for (int64_t g = blockIdx.x; g * 32 < total; g += gridDim.x) {
+    const int64_t q = g * 32 + threadIdx.x;
+    if (q < total) chain_redo_track(a, list[q]);
+  }
+}
+
+// KF_ADAPTIVE's second pass without a list (no scratch memory could be had,
+// or more than 2^32 - 1 tracks): each block gathers the marked tracks of its
+// span (gather_marked) and reruns them.
 __global__ void __launch_bounds__(kRedoThreads) chain_redo_kernel(const ChainArgs a) {
   __shared__ uint16_t list[kRedoSpan];
   __shared__ int count;
   const int64_t span0 = (int64_t)blockIdx.x * kRedoSpan;
   const int cnt = gather_marked(a.status, span0, a.n, list, &count);
-  for (int q = threadIdx.x; q < cnt; q += blockDim.x) {
-    const int64_t i = span0 + list[q];
-    const ChainLoc l6 = chain_locate<6>(i, a.n, a.soa, a.lw);
-    const ChainLoc l21 = chain_locate<21>(i, a.n, a.soa, a.lw);
-    const ChainLoc l3 = chain_locate<3>(i, a.n, a.soa, a.lw);
-    float p[6], C[21];
-    for (int c = 0; c < 6; ++c) p[c] = a.state[l6.base + c * l6.stride];
-    for (int e = 0; e < 21; ++e) C[e] = a.cov[l21.base + e * l21.stride];
-    const float qf = (float)a.charge[i];
-    unsigned st = chain_track_fp64(p, C, qf, a.bz, a.L, a.kinds, a.pos, a.hits, a.hit_stride,
-                                   a.hitcovs, a.hc_stride, l3, l6);
-    st |= finite_status(p, C);
-    for (int c = 0; c < 6; ++c) a.state[l6.base + c * l6.stride] = p[c];
-    for (int e = 0; e < 21; ++e) a.cov[l21.base + e * l21.stride] = C[e];
-    a.status[i] = (uint8_t)st;
+  for (int q = threadIdx.x; q < cnt; q += blockDim.x) chain_redo_track(a, span0 + list[q]);
+}
+
+// A stream-ordered memory pool per device for the second pass's list,
+// created on first use and kept (with its memory: release threshold at the
+// maximum) for the life of the process.
+constexpr int kMaxPoolDevices = 64;
+std::mutex g_redo_pool_mu;
+cudaMemPool_t g_redo_pool[kMaxPoolDevices] = {};
+
+bool redo_pool(int dev, cudaMemPool_t *out) {
+  if (dev < 0 || dev >= kMaxPoolDevices) return false;
+  std::lock_guard<std::mutex> lock(g_redo_pool_mu);
+  if (!g_redo_pool[dev]) {
+    cudaMemPoolProps props = {};
+    props.allocType = cudaMemAllocationTypePinned;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = dev;
+    cudaMemPool_t pool = nullptr;
+    if (cudaMemPoolCreate(&pool, &props) != cudaSuccess) {
+      (void)cudaGetLastError();
+      return false;
+    }
+    uint64_t keep = UINT64_MAX;
+    (void)cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+    g_redo_pool[dev] = pool;
   }
+  *out = g_redo_pool[dev];
+  return true;
+}
+
+// Launch the second pass on stream s: over a compacted list when its
+// scratch can be allocated, else per span (the same results).
+int launch_chain_redo(const ChainArgs &a, cudaStream_t s) {
+  const unsigned spans = (unsigned)((a.n + kRedoSpan - 1) / kRedoSpan);
+  int dev = 0, sms = 0;
+  cudaMemPool_t pool = nullptr;
+  void *buf = nullptr;
+  if (a.n < (int64_t)UINT32_MAX && cudaGetDevice(&dev) == cudaSuccess &&
+      staged::sm_count(dev, &sms) == KF_OK && redo_pool(dev, &pool) &&
+      cudaMallocFromPoolAsync(&buf, 4 * (size_t)(a.n + 1), pool, s) == cudaSuccess) {
+    uint32_t *count = static_cast<uint32_t *>(buf), *list = count + 1;
+    if (int rc = check_cuda(cudaMemsetAsync(count, 0, sizeof(uint32_t), s), "cudaMemsetAsync"))
+      return rc;
+    chain_compact_kernel<<<spans, kRedoThreads, 0, s>>>(a.status, a.n, count, list);
+    if (int rc = check_cuda(cudaGetLastError(), "chain compaction launch")) return rc;
+    chain_redo_list_kernel<<<(unsigned)(kRedoListBlocksPerSm * sms), 32, 0, s>>>(a, count, list);
+    if (int rc = check_cuda(cudaGetLastError(), "chain redo pass launch")) return rc;
+    return check_cuda(cudaFreeAsync(buf, s), "cudaFreeAsync");
+  }
+  clear_error();
+  (void)cudaGetLastError();  // a refused allocation is not the caller's error
+  chain_redo_kernel<<<spans, kRedoThreads, 0, s>>>(a);
+  return check_cuda(cudaGetLastError(), "chain redo pass launch");
 }
 
 }  // namespace
@@ -190,6 +290,5 @@ extern "C" int kf_kalman_chain(const kf_params *params, kf_layout layout, float 
   }
   if (int rc = check_cuda(cudaGetLastError(), "chain launch")) return rc;
   if (params->precision != KF_ADAPTIVE) return KF_OK;
-  chain_redo_kernel<<<(unsigned)((d.n + kRedoSpan - 1) / kRedoSpan), kRedoThreads, 0, s>>>(a);
-  return check_cuda(cudaGetLastError(), "chain redo pass launch");
+  return launch_chain_redo(a, s);
 }

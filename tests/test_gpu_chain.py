@@ -250,6 +250,14 @@ def test_adaptive_chain_redo_pass(dev, chain_full):
     assert 0 < int(redone.sum()) < cw.n // 10
     # tracks no layer marked are bitwise the FP32 chain
     assert np.array_equal(ada[0][:, ~redone], f32[0][:, ~redone])
+    # and the redone ones bitwise the all-FP64 chain (the second pass runs
+    # the same double chain from the same inputs, in whatever order it
+    # gathered them)
+    dc.reset()
+    dc.run(kf.KF_FP64)
+    f64 = dc.download()
+    for x, y in zip(ada, f64):
+        assert np.array_equal(x[..., redone], y[..., redone])
     # the oracle on the redone tracks
     idx = np.flatnonzero(redone)
     o_st, o_cv, o_stat = oracle_chain(cw, idx, oracle.FORM_STANDARD)
