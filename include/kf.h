@@ -328,6 +328,12 @@ typedef struct {
  * layer whose update is rejected (KF_S_NOT_PD) leaves the propagated track.
  * Same arithmetic as the single-step calls: chain over one layer equals the
  * single step bit for bit.
+ * Under KF_ADAPTIVE the second pass (the marked tracks' whole chain in
+ * double) takes 4 (n + 1) bytes of device scratch, stream-ordered on
+ * `stream`, from a memory pool the library creates per device on first use
+ * and keeps (its memory included) for the life of the process; when that
+ * allocation fails, or n >= 2^32 - 1, the pass runs without it, with the
+ * same results.
  */
 int kf_kalman_chain(const kf_params *params, kf_layout layout, float *state,
                     float *cov, const int8_t *charge, const float *hits,
