@@ -608,6 +608,20 @@ int kf_set_step_kernel(int32_t mode);
 int kf_set_staged_ctas_per_sm(int32_t ctas);
 
 /*
+ * kf_set_chain_redo -- how kf_kalman_chain's KF_ADAPTIVE second pass runs
+ * the marked tracks, for all later calls in this process (results are the
+ * same, bit for bit):
+ *   KF_CHAIN_REDO_LIST  (default) the whole batch's marked tracks in one
+ *                       compacted list, 32 to a warp (device scratch from
+ *                       the library's pool; per span when it cannot be had)
+ *   KF_CHAIN_REDO_SPAN  each 4,096-track span's marked tracks by one block
+ * Returns KF_ERR_ARG for any other value.
+ */
+#define KF_CHAIN_REDO_LIST 0
+#define KF_CHAIN_REDO_SPAN 1
+int kf_set_chain_redo(int32_t mode);
+
+/*
  * kf_set_device_wait_limit -- how long the compute warps of the staged
  * kernels (KF_STEP_STAGED and the compressed store's staged kernel) wait for
  * a tile before they give up, in polls of the tile's barrier (each poll

@@ -12,6 +12,7 @@
 // kind is uniform across the grid, so the p2z / p2r branch never diverges.
 #include <cuda_runtime.h>
 
+#include <atomic>
 #include <cstdint>
 #include <mutex>
 
@@ -191,6 +192,8 @@ bool redo_pool(int dev, cudaMemPool_t *out) {
   return true;
 }
 
+std::atomic<int> g_chain_redo{KF_CHAIN_REDO_LIST};
+
 // Launch the second pass on stream s: over a compacted list when its
 // scratch can be allocated, else per span (the same results).
 int launch_chain_redo(const ChainArgs &a, cudaStream_t s) {
@@ -198,7 +201,8 @@ int launch_chain_redo(const ChainArgs &a, cudaStream_t s) {
   int dev = 0, sms = 0;
   cudaMemPool_t pool = nullptr;
   void *buf = nullptr;
-  if (a.n < (int64_t)UINT32_MAX && cudaGetDevice(&dev) == cudaSuccess &&
+  if (g_chain_redo.load(std::memory_order_relaxed) == KF_CHAIN_REDO_LIST &&
+      a.n < (int64_t)UINT32_MAX && cudaGetDevice(&dev) == cudaSuccess &&
       staged::sm_count(dev, &sms) == KF_OK && redo_pool(dev, &pool) &&
       cudaMallocFromPoolAsync(&buf, 4 * (size_t)(a.n + 1), pool, s) == cudaSuccess) {
     uint32_t *count = static_cast<uint32_t *>(buf), *list = count + 1;
@@ -218,6 +222,15 @@ int launch_chain_redo(const ChainArgs &a, cudaStream_t s) {
 
 }  // namespace
 }  // namespace kf
+
+extern "C" int kf_set_chain_redo(int32_t mode) {
+  kf::clear_error();
+  if (mode != KF_CHAIN_REDO_LIST && mode != KF_CHAIN_REDO_SPAN)
+    return kf::set_error(KF_ERR_ARG, "chain redo mode %d is neither KF_CHAIN_REDO_LIST nor "
+                         "KF_CHAIN_REDO_SPAN", mode);
+  kf::g_chain_redo.store(mode, std::memory_order_relaxed);
+  return KF_OK;
+}
 
 extern "C" int kf_kalman_chain(const kf_params *params, kf_layout layout, float *state,
                                float *cov, const int8_t *charge, const float *hits,

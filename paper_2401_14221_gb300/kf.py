@@ -144,6 +144,8 @@ def load():
     lib.kf_set_step_kernel.restype = ctypes.c_int
     lib.kf_set_staged_ctas_per_sm.argtypes = [ctypes.c_int32]
     lib.kf_set_staged_ctas_per_sm.restype = ctypes.c_int
+    lib.kf_set_chain_redo.argtypes = [ctypes.c_int32]
+    lib.kf_set_chain_redo.restype = ctypes.c_int
     lib.kf_set_host_path.argtypes = [ctypes.c_int32]
     lib.kf_set_host_path.restype = ctypes.c_int
     lib.kf_set_device_wait_limit.argtypes = [ctypes.c_int64]
@@ -392,6 +394,14 @@ KF_DEVERR_TIMEOUT = 1
 def kf_set_step_kernel(mode: int) -> None:
     """C-ABI kf_set_step_kernel: KF_STEP_AUTO / KF_STEP_DIRECT / KF_STEP_STAGED."""
     _check(load().kf_set_step_kernel(int(mode)))
+
+
+KF_CHAIN_REDO_LIST, KF_CHAIN_REDO_SPAN = 0, 1
+
+
+def kf_set_chain_redo(mode: int) -> None:
+    """C-ABI kf_set_chain_redo: KF_CHAIN_REDO_LIST / KF_CHAIN_REDO_SPAN."""
+    _check(load().kf_set_chain_redo(int(mode)))
 
 
 def kf_set_staged_ctas_per_sm(ctas: int) -> None:

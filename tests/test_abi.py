@@ -81,7 +81,8 @@ def test_process_wide_knobs_validate_their_argument(lib):
     # host state only: an unknown mode is refused and leaves the setting alone
     for fn, bad, good in ((kf.kf_set_host_path, 3, kf.KF_HOST_AUTO),
                           (kf.kf_set_step_kernel, 3, kf.KF_STEP_AUTO),
-                          (kf.kf_set_staged_ctas_per_sm, 4, 0)):
+                          (kf.kf_set_staged_ctas_per_sm, 4, 0),
+                          (kf.kf_set_chain_redo, 2, kf.KF_CHAIN_REDO_LIST)):
         with pytest.raises(kf.KfError) as e:
             fn(bad)
         assert e.value.code == kf.KF_ERR_ARG

@@ -258,6 +258,16 @@ def test_adaptive_chain_redo_pass(dev, chain_full):
     f64 = dc.download()
     for x, y in zip(ada, f64):
         assert np.array_equal(x[..., redone], y[..., redone])
+    # the second pass per span instead of over one compacted list: the same
+    kf.kf_set_chain_redo(kf.KF_CHAIN_REDO_SPAN)
+    try:
+        dc.reset()
+        dc.run(kf.KF_ADAPTIVE)
+        per_span = dc.download()
+    finally:
+        kf.kf_set_chain_redo(kf.KF_CHAIN_REDO_LIST)
+    for x, y in zip(ada, per_span):
+        assert np.array_equal(x, y)
     # the oracle on the redone tracks
     idx = np.flatnonzero(redone)
     o_st, o_cv, o_stat = oracle_chain(cw, idx, oracle.FORM_STANDARD)
