@@ -206,13 +206,18 @@ int launch_chain_redo(const ChainArgs &a, cudaStream_t s) {
       staged::sm_count(dev, &sms) == KF_OK && redo_pool(dev, &pool) &&
       cudaMallocFromPoolAsync(&buf, 4 * (size_t)(a.n + 1), pool, s) == cudaSuccess) {
     uint32_t *count = static_cast<uint32_t *>(buf), *list = count + 1;
-    if (int rc = check_cuda(cudaMemsetAsync(count, 0, sizeof(uint32_t), s), "cudaMemsetAsync"))
-      return rc;
-    chain_compact_kernel<<<spans, kRedoThreads, 0, s>>>(a.status, a.n, count, list);
-    if (int rc = check_cuda(cudaGetLastError(), "chain compaction launch")) return rc;
-    chain_redo_list_kernel<<<(unsigned)(kRedoListBlocksPerSm * sms), 32, 0, s>>>(a, count, list);
-    if (int rc = check_cuda(cudaGetLastError(), "chain redo pass launch")) return rc;
-    return check_cuda(cudaFreeAsync(buf, s), "cudaFreeAsync");
+    int rc = check_cuda(cudaMemsetAsync(count, 0, sizeof(uint32_t), s), "cudaMemsetAsync");
+    if (rc == KF_OK) {
+      chain_compact_kernel<<<spans, kRedoThreads, 0, s>>>(a.status, a.n, count, list);
+      rc = check_cuda(cudaGetLastError(), "chain compaction launch");
+    }
+    if (rc == KF_OK) {
+      chain_redo_list_kernel<<<(unsigned)(kRedoListBlocksPerSm * sms), 32, 0, s>>>(a, count,
+                                                                                  list);
+      rc = check_cuda(cudaGetLastError(), "chain redo pass launch");
+    }
+    const cudaError_t freed = cudaFreeAsync(buf, s);  // returned to the pool on every path
+    return rc != KF_OK ? rc : check_cuda(freed, "cudaFreeAsync");
   }
   clear_error();
   (void)cudaGetLastError();  // a refused allocation is not the caller's error
