@@ -166,15 +166,19 @@ __global__ void __launch_bounds__(kRedoThreads) chain_redo_kernel(const ChainArg
 
 // A stream-ordered memory pool per device for the second pass's list,
 // created on first use and kept (with its memory: release threshold at the
-// maximum) for the life of the process.
+// maximum) for the life of the process.  It is not created while the
+// stream is being captured into a graph (creating a pool is not a
+// capturable call); allocating from an existing pool is, and gives the
+// graph an allocation node.
 constexpr int kMaxPoolDevices = 64;
 std::mutex g_redo_pool_mu;
 cudaMemPool_t g_redo_pool[kMaxPoolDevices] = {};
 
-bool redo_pool(int dev, cudaMemPool_t *out) {
+bool redo_pool(int dev, bool may_create, cudaMemPool_t *out) {
   if (dev < 0 || dev >= kMaxPoolDevices) return false;
   std::lock_guard<std::mutex> lock(g_redo_pool_mu);
   if (!g_redo_pool[dev]) {
+    if (!may_create) return false;
     cudaMemPoolProps props = {};
     props.allocType = cudaMemAllocationTypePinned;
     props.location.type = cudaMemLocationTypeDevice;
@@ -201,9 +205,12 @@ int launch_chain_redo(const ChainArgs &a, cudaStream_t s) {
   int dev = 0, sms = 0;
   cudaMemPool_t pool = nullptr;
   void *buf = nullptr;
+  cudaStreamCaptureStatus capture = cudaStreamCaptureStatusNone;
+  const bool capturing = cudaStreamIsCapturing(s, &capture) != cudaSuccess ||
+                         capture != cudaStreamCaptureStatusNone;
   if (g_chain_redo.load(std::memory_order_relaxed) == KF_CHAIN_REDO_LIST &&
       a.n < (int64_t)UINT32_MAX && cudaGetDevice(&dev) == cudaSuccess &&
-      staged::sm_count(dev, &sms) == KF_OK && redo_pool(dev, &pool) &&
+      staged::sm_count(dev, &sms) == KF_OK && redo_pool(dev, !capturing, &pool) &&
       cudaMallocFromPoolAsync(&buf, 4 * (size_t)(a.n + 1), pool, s) == cudaSuccess) {
     uint32_t *count = static_cast<uint32_t *>(buf), *list = count + 1;
     int rc = check_cuda(cudaMemsetAsync(count, 0, sizeof(uint32_t), s), "cudaMemsetAsync");

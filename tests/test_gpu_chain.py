@@ -217,6 +217,31 @@ def test_adaptive_chain_meets_the_bounds_on_every_track(dev, chain_full):
     parity_log.expect_ok("chain", rep)
 
 
+def test_adaptive_chain_in_a_cuda_graph(dev):
+    # the adaptive chain captured into a CUDA graph (its second pass's list
+    # becomes an allocation node of the graph) replays to the eager result,
+    # bit for bit, twice
+    cw = W.make_chain(events=16, seed=47)
+    dc = kf.chain_upload(cw, kf.KF_AOSOA, 32, dev)
+    dc.run(kf.KF_FP32)
+    f32 = dc.download()
+    dc.reset()
+    dc.run(kf.KF_ADAPTIVE)
+    ref = dc.download()
+    assert np.any(ref[1] != f32[1])  # some tracks went through the second pass
+    g = torch.cuda.CUDAGraph()
+    dc.reset()
+    torch.cuda.synchronize()
+    with torch.cuda.graph(g, stream=torch.cuda.Stream()):
+        dc.run(kf.KF_ADAPTIVE)
+    for _ in range(2):
+        dc.reset()
+        g.replay()
+        torch.cuda.synchronize()
+        for x, y in zip(ref, dc.download()):
+            assert np.array_equal(x, y)
+
+
 def test_empty_chain_and_bad_layers(dev):
     cw = W.make_chain(events=1, seed=43, sizes=np.array([100]))
     dc = kf.chain_upload(cw, kf.KF_SOA, 0, dev)
