@@ -332,8 +332,10 @@ typedef struct {
  * double) takes 4 (n + 1) bytes of device scratch, stream-ordered on
  * `stream`, from a memory pool the library creates per device on first use
  * and keeps (its memory included) for the life of the process; when that
- * allocation fails, or n >= 2^32 - 1, the pass runs without it, with the
- * same results.
+ * allocation fails, or n >= 2^32 - 1, or the pool does not exist yet while
+ * `stream` is being captured into a graph, the pass runs without it, with
+ * the same results.  Under capture the allocation becomes a node of the
+ * graph.
  */
 int kf_kalman_chain(const kf_params *params, kf_layout layout, float *state,
                     float *cov, const int8_t *charge, const float *hits,
